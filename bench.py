@@ -1,0 +1,409 @@
+"""Benchmark of the fused 8x8 T1 block codec on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batch_1024x1024|ragged_2000|video_600x1080p|single_512]
+
+A step is one pass of the whole path -- forward transform, zonal retention
+of the first r zig-zag coefficients, inverse, rounding, reconstruction
+written back, per-image SSE and PSNR -- over every image of the workload,
+with the inputs resident in HBM.  The default workload is 1024 seeded
+1024x1024 u8 AR(1) images with r = 16 (16.8 M blocks, 1 GiB in + 1 GiB
+reconstruction out, larger than L2, so no flush is needed between steps).
+
+Timing: W untimed steps, then K steps between barriers and device
+synchronisation, CUDA events on the launching stream; the max over ranks.
+With N > 1 (torchrun) every rank runs its own replica of the workload
+(weak scaling, no collective on the data path).  Rank 0 prints one JSON
+line.  ``--impl reference`` times the CPU oracle on host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "8×8 blocks/s and HBM GB/s (% of peak), fused fwd+zonal+inv+SSE, bit-exact, 1 GB300"
+UNIT = "blocks/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch_1024x1024",
+                    choices=["batch_1024x1024", "ragged_2000", "video_600x1080p", "single_512"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU-oracle sample budget (seconds of host work)")
+    return ap.parse_args()
+
+
+# ---- distributed plumbing ---------------------------------------------------------------
+
+
+class Dist:
+    def __init__(self, backend: str):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        return self._reduce(v, "max")
+
+    def sum(self, v: float) -> float:
+        return self._reduce(v, "sum")
+
+    def _reduce(self, v, op):
+        if not self.pg:
+            return v
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---- clocks during the timed region -------------------------------------------------------
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "samples": len(self.rows),
+        }
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---- workloads --------------------------------------------------------------------------------
+
+
+class Workload:
+    """Planes of one workload resident on the GPU, with reconstruction buffers."""
+
+    def __init__(self, name: str, device: str):
+        import torch
+
+        from paper_1808_02950_gb300 import synth
+
+        self.name = name
+        self.planes = []  # (img tensor 2-D, r)
+        if name == "batch_1024x1024":
+            imgs, r = synth.batch_1024x1024(device)
+            self.storage = [imgs]
+            self.planes = [(imgs[i], r) for i in range(imgs.shape[0])]
+            self.desc = {"workload": "batch_1024x1024", "images": int(imgs.shape[0]),
+                         "H": 1024, "W": 1024, "dtype": "u8", "r": r, "rho": 0.95}
+        elif name == "single_512":
+            img, r = synth.single_512(device)
+            self.storage = [img]
+            self.planes = [(img, r)]
+            self.desc = {"workload": "single_512", "images": 1, "H": 512, "W": 512, "dtype": "u8",
+                         "r": r, "rho": 0.95}
+        elif name == "ragged_2000":
+            buf, offs, H, W, rr = synth.ragged_2000(device)
+            self.storage = [buf]
+            for i in range(len(offs)):
+                v = buf[int(offs[i]): int(offs[i]) + int(H[i] * W[i])].view(int(H[i]), int(W[i]))
+                self.planes.append((v, int(rr[i])))
+            self.desc = {"workload": "ragged_2000", "images": len(offs), "dtype": "u8",
+                         "H,W": "U{64..4096} step 8", "r": "U{4,8,16,32}"}
+        elif name == "video_600x1080p":
+            Y, U, V = synth.video_600x1080p(device)
+            self.storage = [Y, U, V]
+            for t in range(Y.shape[0]):
+                self.planes += [(Y[t], 16), (U[t], 8), (V[t], 8)]
+            self.desc = {"workload": "video_600x1080p", "frames": int(Y.shape[0]),
+                         "planes": len(self.planes), "dtype": "i16 residual", "r": "Y 16, UV 8"}
+        else:
+            raise ValueError(name)
+        self.recons = [torch.empty_like(p) for p, _ in self.planes]
+        self.blocks = sum(((p.shape[0] + 7) // 8) * ((p.shape[1] + 7) // 8) for p, _ in self.planes)
+        self.in_bytes = sum(p.numel() * p.element_size() for p, _ in self.planes)
+        self.out_bytes = sum(p.numel() * p.element_size() for p in self.recons)
+
+
+def time_ours(args, dist, out):
+    import torch
+
+    import paper_1808_02950_gb300 as P
+
+    dev = f"cuda:{dist.local_rank}"
+    torch.cuda.set_device(dev)
+    wl = Workload(args.workload, dev)
+    planes = P.make_planes([p for p, _ in wl.planes], [r for _, r in wl.planes], wl.recons)
+    n = len(wl.planes)
+    sse = torch.zeros(n, dtype=torch.int64, device=dev)
+    psnr = torch.zeros(n, dtype=torch.float64, device=dev)
+    plan = P.tdct_plan_create(planes)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        plan.launch(sse, psnr, stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        plan.launch(sse, psnr, stream)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    total_ms = dist.max(total_ms)
+    blocks_all = dist.sum(wl.blocks)
+    value = blocks_all * args.steps / (total_ms / 1e3)
+    step_ms = total_ms / args.steps
+
+    # Roofline of the dominant kernel (the fused codec): algorithmic bytes =
+    # samples read once + reconstruction written once (+ 16 B per image).
+    algo_bytes = wl.in_bytes + wl.out_bytes + 16 * n
+    kernel_ms = statistics.mean(per_step)
+    peak, peak_kind = measured_peaks()
+    achieved = algo_bytes / (kernel_ms / 1e3) / 1e9
+    out.update({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 (u8 in/out)", "data": "synthetic",
+        "config": {**wl.desc, "parallelism": f"replicas{dist.world}", "path": "butterfly",
+                   "l2": "inputs larger than L2 (no flush)" if algo_bytes > 256e6 else
+                   "inputs smaller than L2"},
+        "hbm_gbs": achieved,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "algo_bytes_per_launch": algo_bytes, "kernel_ms": kernel_ms},
+        "clocks": clk,
+        "gpu_launches": plan.kernel_count() * args.steps,
+    })
+
+    # End to end through the public call with host buffers: every step copies
+    # the inputs from pinned host memory, runs tdct_codec_error_batched and
+    # reads the per-image SSE and PSNR back.
+    if not args.no_e2e:
+        host_bufs = [s.cpu().pin_memory() for s in wl.storage]
+        sse_h = torch.empty(n, dtype=torch.int64).pin_memory()
+        psnr_h = torch.empty(n, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            for hb, db in zip(host_bufs, wl.storage):
+                db.copy_(hb, non_blocking=True)
+            P.tdct_codec_error_batched(planes, sse, psnr, stream=stream)
+            sse_h.copy_(sse, non_blocking=True)
+            psnr_h.copy_(psnr, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        ke = max(3, min(args.steps, 10))
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        e_ms = dist.max(e0.elapsed_time(e1))
+        out["e2e"] = {"value": blocks_all * ke / (e_ms / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(wl.in_bytes), "d2h_bytes_per_step": 16 * n,
+                      "steps": ke}
+    plan.close()
+    return wl
+
+
+def cpu_oracle_rate(planes_host, budget_s: float):
+    """Run the oracle over host planes with one thread per core until the
+    budget is spent; returns (blocks/s, blocks done, threads, planes done)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import codec as oc
+    from oracle import matrices as M
+
+    oc.lib()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    done_blocks = 0
+    done_planes = 0
+    lock = threading.Lock()
+    idx = [0]
+
+    def worker():
+        nonlocal done_blocks, done_planes
+        while True:
+            with lock:
+                if idx[0] >= len(planes_host) or time.perf_counter() - t0 > budget_s:
+                    return
+                i = idx[0]
+                idx[0] += 1
+            img, r = planes_host[i]
+            oc.codec_plane(img, M.T1, r)
+            nb = ((img.shape[0] + 7) // 8) * ((img.shape[1] + 7) // 8)
+            with lock:
+                done_blocks += nb
+                done_planes += 1
+
+    with ThreadPoolExecutor(cores) as ex:
+        for f in [ex.submit(worker) for _ in range(cores)]:
+            f.result()
+    dt = time.perf_counter() - t0
+    return done_blocks / dt, done_blocks, cores, done_planes
+
+
+def host_sample(wl, max_planes: int):
+    """Copy an evenly spaced sample of the workload's planes to host memory."""
+    n = len(wl.planes)
+    step = max(1, n // max_planes)
+    return [(wl.planes[i][0].cpu().numpy(), wl.planes[i][1]) for i in range(0, n, step)][:max_planes]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return main_reference(args)
+    import torch  # noqa: F401
+
+    backend = "nccl" if args.gpus > 1 or int(os.environ.get("WORLD_SIZE", "1")) > 1 else "gloo"
+    dist = Dist(backend)
+    out = {}
+    wl = time_ours(args, dist, out)
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        sample = host_sample(wl, 256)
+        rate, nb, cores, npl = cpu_oracle_rate(sample, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{npl} of {len(wl.planes)} planes ({nb} blocks), "
+                                         f"C oracle (int64 definition), one thread per core"}
+    if dist.rank == 0:
+        print(json.dumps(out))
+    dist.close()
+
+
+def main_reference(args):
+    """The oracle as it stands, timed on host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+
+    from oracle import codec as oc
+
+    oc.lib()
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    wl = Workload(args.workload, dev)
+    sample = host_sample(wl, 64)
+    per_step_budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sample, per_step_budget)
+    rates, blocks, cores, planes = [], 0, 1, 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rate, nb, cores, npl = cpu_oracle_rate(sample, per_step_budget)
+        rates.append(rate)
+        blocks += nb
+        planes += npl
+    wall = time.perf_counter() - t0
+    value = blocks / wall
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {**wl.desc, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{planes} plane runs over {len(sample)} sampled planes, "
+                                   f"{per_step_budget:.1f} s budget per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

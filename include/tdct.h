@@ -1,0 +1,181 @@
+/*
+ * tdct.h -- C ABI of the GB300 library for the 8x8 approximate-DCT block
+ * codec of Oliveira et al., "Low-complexity 8-point DCT approximation based
+ * on angle similarity for image and video coding" (arXiv 1808.02950).
+ *
+ * The path (§6.1 of the paper): every 8x8 block A of a plane is transformed
+ * as B = C_hat A C_hat^T with C_hat = S T (Eq. (1)), S = sqrt((T T^T)^-1)
+ * (Eq. (2)); the first r coefficients of the zig-zag scan are kept and the
+ * rest zeroed; the block is reconstructed as C_hat^T B' C_hat; the
+ * reconstruction is compared with the original (SSE / PSNR).
+ *
+ * Arguments are plain pointers and sizes.  Conventions for every call:
+ *   - "d_" pointers are CUDA device pointers owned by the caller; the host
+ *     arrays T and n are read before the call returns.
+ *   - T is the 8x8 low-complexity matrix, row-major int8 (row k = t_k^T,
+ *     §3.1 Eq. (4)); n are the 8 squared row norms, n_k = (T T^T)_kk, i.e.
+ *     S = diag(1/sqrt(n_k)) as §4.1 states it for T1.  The library checks
+ *     that T T^T == diag(n) and returns TDCT_ENOTORTHO otherwise.  The fused
+ *     GPU path implements the paper's T1 (§4.1, fast algorithm of §5.1);
+ *     another orthogonal T returns TDCT_EUNSUPPORTED.
+ *   - Planes are row-major with a row pitch in BYTES.  dtype TDCT_U8 holds
+ *     8-bit samples (images), TDCT_I16 holds int16 residual samples in
+ *     [-255, 255].  H and W are in samples and need not be multiples of 8:
+ *     edge blocks are zero padded and padded samples do not enter the SSE.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and never synchronise it.  Host-side argument errors
+ *     are returned before anything is enqueued.  No exception crosses the
+ *     ABI and nothing aborts the process.  tdct_last_error() gives a
+ *     thread-local message for the last failing call.
+ *   - Bit-exactness: coefficients Z = T A T^T are integers; the
+ *     reconstruction equals N / L^2 with L = lcm(n) and an integer N, and is
+ *     rounded half away from zero, then clamped to [0, 255] (U8) or
+ *     [-255, 255] (I16).  Every result is identical to the integer
+ *     definition, bit for bit.
+ */
+#ifndef TDCT_H_
+#define TDCT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle; identical to cudaStream_t / CUstream. */
+typedef struct CUstream_st* tdct_stream_t;
+
+enum tdct_status {
+  TDCT_OK = 0,
+  TDCT_EINVAL = 1,       /* bad argument: null pointer, size, r, pitch, dtype */
+  TDCT_ENOTORTHO = 2,    /* T T^T is not diag(n) */
+  TDCT_ECUDA = 3,        /* a CUDA runtime call failed */
+  TDCT_ETIMEOUT = 4,     /* a bounded device wait gave up (see tdct_sync_status) */
+  TDCT_EDEVICE = 5,      /* the device reported an internal check failure */
+  TDCT_ENOMEM = 6,       /* device or host allocation failed */
+  TDCT_EUNSUPPORTED = 7  /* valid request the library does not implement */
+};
+
+enum tdct_dtype { TDCT_U8 = 0, TDCT_I16 = 1 };
+
+enum tdct_precision { TDCT_FP32 = 0, TDCT_BF16 = 1 };
+
+enum tdct_path { TDCT_PATH_AUTO = 0, TDCT_PATH_BUTTERFLY = 1, TDCT_PATH_TC_I8 = 2 };
+
+/*
+ * tdct_forward -- forward 2-D transform of every block (§6.1, B = C_hat A
+ * C_hat^T), returning the integer part Z = T A T^T.
+ *   d_img     plane, H x W samples of `dtype`, row pitch `pitch` bytes
+ *   d_coef    output, int32 [ceil(H/8)][ceil(W/8)][8][8]; element (i, j) of a
+ *             block is Z_ij (i = vertical, j = horizontal frequency).  The
+ *             normalised coefficient is B_ij = Z_ij / sqrt(n_i n_j).
+ * Errors: TDCT_EINVAL (null pointer, H or W < 1, pitch too small, dtype),
+ *         TDCT_ENOTORTHO, TDCT_EUNSUPPORTED, TDCT_ECUDA.
+ */
+int tdct_forward(const void* d_img, int64_t pitch, int H, int W, int dtype,
+                 const int8_t T[64], const int32_t n[8], int32_t* d_coef,
+                 tdct_stream_t stream);
+
+/*
+ * tdct_zonal_inverse -- zonal retention of the first r zig-zag coefficients
+ * and inverse 2-D transform (§6.1, A = C_hat^T B' C_hat) of every block.
+ *   d_coef    int32 Z as written by tdct_forward ([nby][nbx][8][8])
+ *   r         retained coefficients, 1..64
+ *   d_out     reconstruction, H x W samples of `dtype`, pitch `out_pitch`
+ * Errors: as tdct_forward, plus TDCT_EINVAL for r outside 1..64.
+ */
+int tdct_zonal_inverse(const int32_t* d_coef, int H, int W, int dtype,
+                       const int8_t T[64], const int32_t n[8], int r, void* d_out,
+                       int64_t out_pitch, tdct_stream_t stream);
+
+/*
+ * tdct_codec_error -- the fused codec of one plane: forward, zonal r,
+ * inverse, rounding, and the reconstruction error (§6.1).  Each sample is
+ * read from HBM once; the reconstruction is written once if requested.
+ *   d_recon   reconstruction output or NULL (error only)
+ *   d_sse     output, one uint64: sum over valid samples of (a - a')^2
+ *   d_psnr    output or NULL, one double: 10 log10(255^2 H W / SSE),
+ *             +inf when SSE = 0
+ * Errors: as tdct_zonal_inverse.
+ */
+int tdct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype,
+                     const int8_t T[64], const int32_t n[8], int r, void* d_recon,
+                     int64_t recon_pitch, uint64_t* d_sse, double* d_psnr,
+                     tdct_stream_t stream);
+
+/* One plane of a ragged batch (device pointers, per-plane r and dtype). */
+typedef struct tdct_plane {
+  const void* img;     /* device pointer to sample (0, 0) */
+  int64_t pitch;       /* row pitch in bytes */
+  int32_t H, W;        /* size in samples, >= 1 */
+  int32_t r;           /* retained zig-zag coefficients, 1..64 */
+  int32_t dtype;       /* TDCT_U8 or TDCT_I16 */
+  void* recon;         /* device pointer or NULL */
+  int64_t recon_pitch; /* row pitch in bytes of recon */
+} tdct_plane;
+
+/*
+ * tdct_codec_error_batched -- tdct_codec_error over a ragged batch of planes
+ * (different sizes, r and dtype) in one enqueue: the library builds a
+ * block-offset table, stages it in stream-ordered device memory and runs
+ * persistent kernels over all planes.
+ *   planes    host array of nplanes descriptors (1 <= nplanes <= 2^20)
+ *   d_sse     output, uint64 [nplanes]
+ *   d_psnr    output or NULL, double [nplanes]
+ *   path      TDCT_PATH_AUTO or TDCT_PATH_BUTTERFLY
+ * Errors: as tdct_codec_error for any plane, TDCT_ENOMEM.
+ */
+int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                             const int32_t n[8], uint64_t* d_sse, double* d_psnr,
+                             int path, tdct_stream_t stream);
+
+/*
+ * Batch plans: the same work as tdct_codec_error_batched, prepared once
+ * (validation, block-offset table in device memory, launch configuration)
+ * and replayed as one CUDA graph per launch.  The plan owns its device
+ * memory until tdct_plan_destroy.  Planes' pointers are fixed at creation.
+ */
+typedef struct tdct_plan tdct_plan;
+
+int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                     const int32_t n[8], int path, tdct_plan** out_plan);
+/* Enqueue one run of the plan on `stream`: SSE (and PSNR) for every plane. */
+int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stream_t stream);
+/* Kernel launches one tdct_plan_launch performs (for launch accounting). */
+int tdct_plan_kernel_count(const tdct_plan* plan);
+void tdct_plan_destroy(tdct_plan* plan);
+
+/*
+ * tdct_dct_codec_error -- the exact-DCT comparison codec (§6.1 with C the
+ * orthonormal 8-point DCT-II of §2, C[k][j] = c_k cos(pi (2j+1) k / 16)).
+ *   precision TDCT_FP32: FP32 constants, FP32 arithmetic.
+ *             TDCT_BF16: constants and inter-stage values rounded to bf16,
+ *             products accumulated in FP32 (the numerics of a bf16 GEMM).
+ *   d_coef    output or NULL: float [nby][nbx][8][8], Y = C A C^T
+ *   Rounding and clamping as the integer path.  Results are close to, not
+ *   identical with, the FP64 definition.
+ */
+int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype, int r,
+                         int precision, float* d_coef, void* d_recon, int64_t recon_pitch,
+                         uint64_t* d_sse, double* d_psnr, tdct_stream_t stream);
+
+/*
+ * Device status word: a bounded device-side wait that gives up, or an
+ * internal consistency check, records a code instead of trapping.  This
+ * synchronises `stream`, returns TDCT_OK, TDCT_ETIMEOUT or TDCT_EDEVICE and
+ * clears the word.
+ */
+int tdct_sync_status(tdct_stream_t stream);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* tdct_last_error(void);
+
+/* Library version string. */
+const char* tdct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDCT_H_ */

@@ -1,0 +1,238 @@
+"""ctypes binding of libtdct (include/tdct.h): the same names, marshalling only.
+
+Every function takes device tensors (torch, for memory and streams) or plain
+integers, converts them to pointers and sizes, calls the C entry point and
+raises ``TdctError`` on a non-zero status.  No arithmetic of the codec runs
+here; if the CUDA library cannot be loaded, every call fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+TDCT_OK, TDCT_EINVAL, TDCT_ENOTORTHO, TDCT_ECUDA = 0, 1, 2, 3
+TDCT_ETIMEOUT, TDCT_EDEVICE, TDCT_ENOMEM, TDCT_EUNSUPPORTED = 4, 5, 6, 7
+TDCT_U8, TDCT_I16 = 0, 1
+TDCT_FP32, TDCT_BF16 = 0, 1
+TDCT_PATH_AUTO, TDCT_PATH_BUTTERFLY, TDCT_PATH_TC_I8 = 0, 1, 2
+
+# T1 of §4.1 and n = diag(T1 T1^T), the arguments the paper states (S = diag(1/sqrt(n))).
+T1 = (
+    (1, 1, 1, 1, 1, 1, 1, 1),
+    (2, 2, 1, 0, 0, -1, -2, -2),
+    (2, 1, -1, -2, -2, -1, 1, 2),
+    (1, 0, -2, -2, 2, 2, 0, -1),
+    (1, -1, -1, 1, 1, -1, -1, 1),
+    (2, -2, 0, 1, -1, 0, 2, -2),
+    (1, -2, 2, -1, -1, 2, -2, 1),
+    (0, -1, 2, -2, 2, -2, 1, 0),
+)
+N1 = (8, 18, 20, 18, 8, 18, 20, 18)
+
+EXPORTS = (
+    "tdct_forward", "tdct_zonal_inverse", "tdct_codec_error", "tdct_codec_error_batched",
+    "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_destroy",
+    "tdct_dct_codec_error", "tdct_sync_status", "tdct_last_error", "tdct_version",
+)
+
+
+class TdctError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tdct error {code}: {msg}")
+        self.code = code
+
+
+class TdctPlane(ctypes.Structure):
+    _fields_ = [
+        ("img", ctypes.c_void_p), ("pitch", ctypes.c_int64),
+        ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("r", ctypes.c_int32),
+        ("dtype", ctypes.c_int32), ("recon", ctypes.c_void_p), ("recon_pitch", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libtdct.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libtdct.so is missing at {_build.LIB}; run build()")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.tdct_forward.argtypes = [vp, i64, i32, i32, i32, vp, vp, vp, vp]
+    L.tdct_zonal_inverse.argtypes = [vp, i32, i32, i32, vp, vp, i32, vp, i64, vp]
+    L.tdct_codec_error.argtypes = [vp, i64, i32, i32, i32, vp, vp, i32, vp, i64, vp, vp, vp]
+    L.tdct_codec_error_batched.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
+    L.tdct_plan_create.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_void_p)]
+    L.tdct_plan_launch.argtypes = [vp, vp, vp, vp]
+    L.tdct_plan_kernel_count.argtypes = [vp]
+    L.tdct_plan_destroy.argtypes = [vp]
+    L.tdct_plan_destroy.restype = None
+    L.tdct_dct_codec_error.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp, vp, i64, vp, vp, vp]
+    L.tdct_sync_status.argtypes = [vp]
+    L.tdct_last_error.restype = ctypes.c_char_p
+    L.tdct_version.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("tdct_plan_destroy", "tdct_last_error", "tdct_version"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> None:
+    if rc != TDCT_OK:
+        raise TdctError(rc, load().tdct_last_error().decode())
+
+
+def _T_n(T=None, n=None):
+    T = T1 if T is None else T
+    n = N1 if n is None else n
+    flat = [int(v) for row in T for v in row]
+    tb = (ctypes.c_int8 * 64)(*flat)
+    nb = (ctypes.c_int32 * 8)(*[int(v) for v in n])
+    return tb, nb
+
+
+def _ptr(t) -> int | None:
+    """Device address of a tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _plane_info(img):
+    """(dtype code, H, W, pitch bytes) of a 2-D uint8 / int16 tensor."""
+    import torch
+
+    if img.dim() != 2:
+        raise ValueError("planes are 2-D tensors")
+    if img.dtype == torch.uint8:
+        dt = TDCT_U8
+    elif img.dtype == torch.int16:
+        dt = TDCT_I16
+    else:
+        raise TypeError("planes are uint8 or int16")
+    if img.stride(1) != 1:
+        raise ValueError("plane rows must be contiguous")
+    return dt, img.shape[0], img.shape[1], img.stride(0) * img.element_size()
+
+
+def tdct_version() -> str:
+    return load().tdct_version().decode()
+
+
+def tdct_forward(img, coef, T=None, n=None, stream=None) -> None:
+    dt, H, W, pitch = _plane_info(img)
+    tb, nb = _T_n(T, n)
+    _check(load().tdct_forward(_ptr(img), pitch, H, W, dt, tb, nb, _ptr(coef), _stream(stream)))
+
+
+def tdct_zonal_inverse(coef, r: int, out, T=None, n=None, stream=None) -> None:
+    dt, H, W, pitch = _plane_info(out)
+    tb, nb = _T_n(T, n)
+    _check(load().tdct_zonal_inverse(_ptr(coef), H, W, dt, tb, nb, int(r), _ptr(out), pitch,
+                                     _stream(stream)))
+
+
+def tdct_codec_error(img, r: int, sse, recon=None, psnr=None, T=None, n=None, stream=None) -> None:
+    dt, H, W, pitch = _plane_info(img)
+    rp = _plane_info(recon)[3] if recon is not None else 0
+    tb, nb = _T_n(T, n)
+    _check(load().tdct_codec_error(_ptr(img), pitch, H, W, dt, tb, nb, int(r), _ptr(recon), rp,
+                                   _ptr(sse), _ptr(psnr), _stream(stream)))
+
+
+def make_planes(imgs, rs, recons=None):
+    """ctypes array of tdct_plane from lists of 2-D tensors and retentions."""
+    arr = (TdctPlane * len(imgs))()
+    for i, img in enumerate(imgs):
+        dt, H, W, pitch = _plane_info(img)
+        rec = recons[i] if recons is not None else None
+        arr[i] = TdctPlane(_ptr(img), pitch, H, W, int(rs[i]), dt, _ptr(rec),
+                           _plane_info(rec)[3] if rec is not None else 0)
+    return arr
+
+
+def make_planes_raw(rows):
+    """ctypes array of tdct_plane from (img_ptr, pitch, H, W, r, dtype, recon_ptr, recon_pitch)."""
+    arr = (TdctPlane * len(rows))()
+    for i, row in enumerate(rows):
+        arr[i] = TdctPlane(*row)
+    return arr
+
+
+def tdct_codec_error_batched(planes, sse, psnr=None, path=TDCT_PATH_AUTO, T=None, n=None,
+                             stream=None) -> None:
+    tb, nb = _T_n(T, n)
+    _check(load().tdct_codec_error_batched(ctypes.addressof(planes), len(planes), tb, nb,
+                                           _ptr(sse), _ptr(psnr), int(path), _stream(stream)))
+
+
+class TdctPlan:
+    """Owner of a tdct_plan (tdct_plan_create / _launch / _destroy)."""
+
+    def __init__(self, planes, path=TDCT_PATH_AUTO, T=None, n=None):
+        tb, nb = _T_n(T, n)
+        h = ctypes.c_void_p()
+        _check(load().tdct_plan_create(ctypes.addressof(planes), len(planes), tb, nb, int(path),
+                                       ctypes.byref(h)))
+        self._h = h
+        self.nplanes = len(planes)
+        self._planes = planes
+
+    def launch(self, sse, psnr=None, stream=None) -> None:
+        _check(load().tdct_plan_launch(self._h, _ptr(sse), _ptr(psnr), _stream(stream)))
+
+    def kernel_count(self) -> int:
+        return load().tdct_plan_kernel_count(self._h)
+
+    def close(self) -> None:
+        if self._h:
+            load().tdct_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tdct_plan_create(planes, path=TDCT_PATH_AUTO, T=None, n=None) -> TdctPlan:
+    return TdctPlan(planes, path, T, n)
+
+
+def tdct_dct_codec_error(img, r: int, sse, precision=TDCT_FP32, coef=None, recon=None, psnr=None,
+                         stream=None) -> None:
+    dt, H, W, pitch = _plane_info(img)
+    rp = _plane_info(recon)[3] if recon is not None else 0
+    _check(load().tdct_dct_codec_error(_ptr(img), pitch, H, W, dt, int(r), int(precision),
+                                       _ptr(coef), _ptr(recon), rp, _ptr(sse), _ptr(psnr),
+                                       _stream(stream)))
+
+
+def tdct_sync_status(stream=None) -> None:
+    _check(load().tdct_sync_status(_stream(stream)))

@@ -1,0 +1,555 @@
+// tdct_abi.cu -- the extern "C" boundary of libtdct (declared in include/tdct.h).
+//
+// Host side: argument validation, the block-offset tables of ragged batches,
+// launch dispatch over the compiled r-classes, batch plans replayed as CUDA
+// graphs, the device status word.  Also the small non-fused kernels: the
+// forward-only and inverse-only transforms and the FP64 PSNR finalisation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/tdct.h"
+#include "tdct_classes.h"
+#include "tdct_dct.h"
+#include "tdct_kernels.cuh"
+
+namespace tdct {
+
+// Instantiated in tdct_inst_*.cu.
+#define TDCT_EXTERN(R)                                                                       \
+  extern template cudaError_t launch_codec<R, 0>(const PlaneTable&, const CodecParams&,      \
+                                                 unsigned long long*, int, cudaStream_t);    \
+  extern template cudaError_t launch_codec<R, 1>(const PlaneTable&, const CodecParams&,      \
+                                                 unsigned long long*, int, cudaStream_t);
+TDCT_FOR_EACH_CLASS(TDCT_EXTERN)
+#undef TDCT_EXTERN
+
+// Device status word (bounded waits and internal checks record a code here).
+__device__ int g_status;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(TDCT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// T1 of §4.1, row-major.
+constexpr int8_t kT1[64] = {
+    1, 1, 1,  1,  1,  1,  1,  1,  2, 2,  1,  0,  0,  -1, -2, -2, 2, 1,  -1, -2, -2, -1,
+    1, 2, 1,  0,  -2, -2, 2,  2,  0, -1, 1,  -1, -1, 1,  1,  -1, -1, 1, 2,  -2, 0,  1,
+    -1, 0, 2, -2, 1,  -2, 2,  -1, -1, 2, -2, 1,  0,  -1, 2,  -2, 2,  -2, 1, 0};
+
+// T T^T == diag(n) (Eq. (2) with a diagonal S), and T == T1 for the fused path.
+int check_transform(const int8_t* T, const int32_t* n) {
+  if (!T || !n) return fail(TDCT_EINVAL, "T and n must not be NULL");
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b) {
+      int64_t dot = 0;
+      for (int l = 0; l < 8; ++l) dot += (int64_t)T[a * 8 + l] * T[b * 8 + l];
+      const int64_t want = a == b ? n[a] : 0;
+      if (dot != want)
+        return fail(TDCT_ENOTORTHO, "(T T^T)[%d][%d] = %lld but diag(n) gives %lld", a, b,
+                    (long long)dot, (long long)want);
+    }
+  if (std::memcmp(T, kT1, 64) != 0)
+    return fail(TDCT_EUNSUPPORTED,
+                "the fused GPU path implements T1 (its fast algorithm); other orthogonal T are "
+                "not implemented");
+  return TDCT_OK;
+}
+
+int sample_bytes(int dtype) { return dtype == TDCT_I16 ? 2 : 1; }
+
+int check_plane(const void* img, int64_t pitch, int H, int W, int dtype, const char* what) {
+  if (dtype != TDCT_U8 && dtype != TDCT_I16) return fail(TDCT_EINVAL, "%s: bad dtype %d", what, dtype);
+  if (!img) return fail(TDCT_EINVAL, "%s: NULL plane pointer", what);
+  if (H < 1 || W < 1 || H > (1 << 28) || W > (1 << 28))
+    return fail(TDCT_EINVAL, "%s: bad size %d x %d", what, H, W);
+  if (pitch < (int64_t)W * sample_bytes(dtype))
+    return fail(TDCT_EINVAL, "%s: pitch %lld < W * sample size", what, (long long)pitch);
+  if (dtype == TDCT_I16 && ((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch) & 1))
+    return fail(TDCT_EINVAL, "%s: int16 plane must be 2-byte aligned", what);
+  return TDCT_OK;
+}
+
+int check_r(int r) {
+  if (r < 1 || r > 64) return fail(TDCT_EINVAL, "r = %d outside 1..64", r);
+  return TDCT_OK;
+}
+
+CodecParams make_params(int r) {
+  CodecParams cp;
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) cp.cmul[8 * i + j] = kept(r, i, j) ? q_of(i) * q_of(j) : 0;
+  return cp;
+}
+
+bool aligned8(const void* p, int64_t pitch) {
+  return ((reinterpret_cast<uintptr_t>(p) | (uintptr_t)pitch) & 7) == 0;
+}
+
+PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int r, void* recon,
+                    int64_t recon_pitch, int slot) {
+  PlaneDesc d;
+  std::memset(&d, 0, sizeof d);
+  d.img = static_cast<const uint8_t*>(img);
+  d.recon = static_cast<uint8_t*>(recon);
+  d.pitch = pitch;
+  d.recon_pitch = recon_pitch;
+  d.H = H;
+  d.W = W;
+  d.nbx = (W + 7) / 8;
+  d.nby = (H + 7) / 8;
+  d.chunks = (d.nbx + 63) / 64;
+  d.dtype = dtype;
+  d.r = r;
+  d.vec16 = (aligned8(img, pitch) ? 1 : 0) | ((recon && aligned8(recon, recon_pitch)) ? 2 : 0);
+  d.slot = slot;
+  return d;
+}
+
+int64_t units_of(const PlaneDesc& d) { return (int64_t)d.nby * d.chunks; }
+
+cudaError_t dispatch_codec(int r, int dtype, const PlaneTable& tab, unsigned long long* sse,
+                           int max_ctas, cudaStream_t s) {
+  const CodecParams cp = make_params(r);
+  switch (r_class(r)) {
+#define TDCT_CASE(R)                                                     \
+  case R:                                                                \
+    return dtype == TDCT_U8 ? launch_codec<R, 0>(tab, cp, sse, max_ctas, s) \
+                            : launch_codec<R, 1>(tab, cp, sse, max_ctas, s);
+    TDCT_FOR_EACH_CLASS(TDCT_CASE)
+#undef TDCT_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+// ---- forward / inverse only kernels ------------------------------------------
+
+template <int DT>
+__global__ void __launch_bounds__(128) forward_kernel(const PlaneDesc P, int32_t* __restrict__ coef,
+                                                      int coef_vec) {
+  const int64_t nb = (int64_t)P.nbx * P.nby;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int by = (int)(b / P.nbx), bx = (int)(b - (int64_t)by * P.nbx);
+    const bool interior = (by * 8 + 8 <= P.H) && ((bx + 1) * 8 <= P.W) && (P.vec16 & 1);
+    RowWords<DT> rw;
+    load_block<DT>(P, by, bx, interior, rw);
+    uint32_t x[64], z[64];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) unpack_row<DT>(rw, k, x + 8 * k);
+    fwd2d<uint32_t>(x, z);
+    int32_t* dst = coef + b * 64;
+    if (coef_vec) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        reinterpret_cast<int4*>(dst)[i] =
+            make_int4((int)z[4 * i], (int)z[4 * i + 1], (int)z[4 * i + 2], (int)z[4 * i + 3]);
+    } else {
+#pragma unroll
+      for (int p = 0; p < 64; ++p) dst[p] = (int32_t)z[p];
+    }
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(128) inverse_kernel(const int32_t* __restrict__ coef,
+                                                      const PlaneDesc P, const CodecParams cp,
+                                                      int coef_vec) {
+  const int64_t nb = (int64_t)P.nbx * P.nby;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int by = (int)(b / P.nbx), bx = (int)(b - (int64_t)by * P.nbx);
+    const int32_t* src = coef + b * 64;
+    uint32_t w[64];
+    if (coef_vec) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int4 v = __ldg(reinterpret_cast<const int4*>(src) + i);
+        w[4 * i] = (uint32_t)v.x;
+        w[4 * i + 1] = (uint32_t)v.y;
+        w[4 * i + 2] = (uint32_t)v.z;
+        w[4 * i + 3] = (uint32_t)v.w;
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < 64; ++p) w[p] = (uint32_t)__ldg(src + p);
+    }
+#pragma unroll
+    for (int p = 0; p < 64; ++p) w[p] *= (uint32_t)cp.cmul[p];
+    int32_t out[64];
+    reconstruct<DT>(w, out);
+    const bool fast = (by * 8 + 8 <= P.H) && ((bx + 1) * 8 <= P.W) && (P.vec16 & 2);
+    store_block<DT>(P, by, bx, fast, out);
+  }
+}
+
+// PSNR = 10 log10(255^2 npix / SSE) in FP64; +inf when SSE = 0 (§6.1).
+__global__ void psnr_kernel(const unsigned long long* __restrict__ sse,
+                            const int64_t* __restrict__ npix, int64_t npix_one,
+                            double* __restrict__ psnr, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long s = sse[i];
+  const double np = (double)(npix ? npix[i] : npix_one);
+  psnr[i] = s == 0ull ? (double)INFINITY : 10.0 * log10(65025.0 * np / (double)s);
+}
+
+namespace {
+
+int grid_for(int64_t items, int threads) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t g = (items + threads - 1) / threads;
+  const int64_t cap = (int64_t)sms * 16;
+  if (g > cap) g = cap;
+  return (int)std::max<int64_t>(g, 1);
+}
+
+// A ragged batch as per-(dtype, r) groups, each a contiguous slice of the
+// descriptor array with its own unit prefix sums.
+struct Group {
+  int dtype, r;
+  int first, count;
+  int64_t units;
+};
+
+int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& descs,
+                std::vector<Group>& groups, std::vector<int64_t>& npix) {
+  if (!planes || nplanes < 1 || nplanes > (1 << 20))
+    return fail(TDCT_EINVAL, "nplanes = %d outside 1..2^20 (or planes is NULL)", nplanes);
+  std::map<std::pair<int, int>, std::vector<int>> by_key;
+  npix.resize(nplanes);
+  for (int i = 0; i < nplanes; ++i) {
+    const tdct_plane& p = planes[i];
+    char what[64];
+    std::snprintf(what, sizeof what, "plane %d", i);
+    int rc = check_plane(p.img, p.pitch, p.H, p.W, p.dtype, what);
+    if (rc) return rc;
+    if (p.r < 1 || p.r > 64) return fail(TDCT_EINVAL, "plane %d: r = %d outside 1..64", i, p.r);
+    if (p.recon && p.recon_pitch < (int64_t)p.W * sample_bytes(p.dtype))
+      return fail(TDCT_EINVAL, "plane %d: recon pitch too small", i);
+    by_key[{p.dtype, p.r}].push_back(i);
+    npix[i] = (int64_t)p.H * p.W;
+  }
+  descs.clear();
+  groups.clear();
+  for (auto& kv : by_key) {
+    Group g{kv.first.first, kv.first.second, (int)descs.size(), (int)kv.second.size(), 0};
+    for (int i : kv.second) {
+      const tdct_plane& p = planes[i];
+      PlaneDesc d = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, p.r, p.recon, p.recon_pitch, i);
+      d.unit_begin = g.units;
+      g.units += units_of(d);
+      descs.push_back(d);
+    }
+    groups.push_back(g);
+  }
+  return TDCT_OK;
+}
+
+// Enqueue the kernels of a batch whose descriptors live at d_descs (device).
+cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_descs,
+                          const int64_t* d_npix, int nplanes, unsigned long long* sse,
+                          double* psnr, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long) * nplanes, s);
+  if (e != cudaSuccess) return e;
+  for (const Group& g : groups) {
+    PlaneTable tab;
+    std::memset(&tab, 0, sizeof tab);
+    tab.d = d_descs + g.first;
+    tab.n = g.count;
+    tab.total_units = g.units;
+    if ((e = dispatch_codec(g.r, g.dtype, tab, sse, 0, s)) != cudaSuccess) return e;
+  }
+  if (psnr) {
+    psnr_kernel<<<(nplanes + 255) / 256, 256, 0, s>>>(sse, d_npix, 0, psnr, nplanes);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace tdct
+
+using namespace tdct;
+
+// ---- plans ----------------------------------------------------------------------
+
+struct tdct_plan {
+  std::vector<Group> groups;
+  int nplanes = 0;
+  PlaneDesc* d_descs = nullptr;
+  int64_t* d_npix = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long* exec_sse = nullptr;
+  double* exec_psnr = nullptr;
+  std::mutex mu;
+};
+
+extern "C" {
+
+const char* tdct_last_error(void) { return g_err.c_str(); }
+
+const char* tdct_version(void) { return "tdct 0.1 (sm_103a)"; }
+
+int tdct_forward(const void* d_img, int64_t pitch, int H, int W, int dtype, const int8_t T[64],
+                 const int32_t n[8], int32_t* d_coef, tdct_stream_t stream) {
+  int rc = check_transform(T, n);
+  if (rc) return rc;
+  if ((rc = check_plane(d_img, pitch, H, W, dtype, "tdct_forward"))) return rc;
+  if (!d_coef || (reinterpret_cast<uintptr_t>(d_coef) & 3))
+    return fail(TDCT_EINVAL, "tdct_forward: d_coef NULL or not 4-byte aligned");
+  const PlaneDesc P = make_desc(d_img, pitch, H, W, dtype, 64, nullptr, 0, 0);
+  const int vec = (reinterpret_cast<uintptr_t>(d_coef) & 15) == 0;
+  const int grid = grid_for((int64_t)P.nbx * P.nby, 128);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (dtype == TDCT_U8) forward_kernel<0><<<grid, 128, 0, s>>>(P, d_coef, vec);
+  else forward_kernel<1><<<grid, 128, 0, s>>>(P, d_coef, vec);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TDCT_OK : cuda_fail(e, "tdct_forward launch");
+}
+
+int tdct_zonal_inverse(const int32_t* d_coef, int H, int W, int dtype, const int8_t T[64],
+                       const int32_t n[8], int r, void* d_out, int64_t out_pitch,
+                       tdct_stream_t stream) {
+  int rc = check_transform(T, n);
+  if (rc) return rc;
+  if ((rc = check_r(r))) return rc;
+  if ((rc = check_plane(d_out, out_pitch, H, W, dtype, "tdct_zonal_inverse"))) return rc;
+  if (!d_coef || (reinterpret_cast<uintptr_t>(d_coef) & 3))
+    return fail(TDCT_EINVAL, "tdct_zonal_inverse: d_coef NULL or not 4-byte aligned");
+  const PlaneDesc P = make_desc(d_out, out_pitch, H, W, dtype, r, d_out, out_pitch, 0);
+  const int vec = (reinterpret_cast<uintptr_t>(d_coef) & 15) == 0;
+  const int grid = grid_for((int64_t)P.nbx * P.nby, 128);
+  const CodecParams cp = make_params(r);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (dtype == TDCT_U8) inverse_kernel<0><<<grid, 128, 0, s>>>(d_coef, P, cp, vec);
+  else inverse_kernel<1><<<grid, 128, 0, s>>>(d_coef, P, cp, vec);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TDCT_OK : cuda_fail(e, "tdct_zonal_inverse launch");
+}
+
+int tdct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype,
+                     const int8_t T[64], const int32_t n[8], int r, void* d_recon,
+                     int64_t recon_pitch, uint64_t* d_sse, double* d_psnr,
+                     tdct_stream_t stream) {
+  int rc = check_transform(T, n);
+  if (rc) return rc;
+  if ((rc = check_r(r))) return rc;
+  if ((rc = check_plane(d_img, pitch, H, W, dtype, "tdct_codec_error"))) return rc;
+  if (d_recon && (rc = check_plane(d_recon, recon_pitch, H, W, dtype, "recon"))) return rc;
+  if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
+    return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
+  if (d_psnr && (reinterpret_cast<uintptr_t>(d_psnr) & 7))
+    return fail(TDCT_EINVAL, "d_psnr not 8-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  PlaneTable tab;
+  std::memset(&tab, 0, sizeof tab);
+  tab.d = nullptr;
+  tab.n = 1;
+  tab.one = make_desc(d_img, pitch, H, W, dtype, r, d_recon, recon_pitch, 0);
+  tab.total_units = units_of(tab.one);
+  unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
+  cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error memset");
+  if ((e = dispatch_codec(r, dtype, tab, sse, 0, s)) != cudaSuccess)
+    return cuda_fail(e, "tdct_codec_error launch");
+  if (d_psnr) {
+    psnr_kernel<<<1, 32, 0, s>>>(sse, nullptr, (int64_t)H * W, d_psnr, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "psnr launch");
+  }
+  return TDCT_OK;
+}
+
+int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                             const int32_t n[8], uint64_t* d_sse, double* d_psnr, int path,
+                             tdct_stream_t stream) {
+  int rc = check_transform(T, n);
+  if (rc) return rc;
+  if (path != TDCT_PATH_AUTO && path != TDCT_PATH_BUTTERFLY)
+    return fail(TDCT_EUNSUPPORTED, "path %d is not implemented for batches", path);
+  if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
+    return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
+  std::vector<PlaneDesc> descs;
+  std::vector<Group> groups;
+  std::vector<int64_t> npix;
+  if ((rc = build_batch(planes, nplanes, descs, groups, npix))) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // Stream-ordered scratch for the block-offset table, freed after the kernels.
+  const size_t bytes_desc = sizeof(PlaneDesc) * descs.size();
+  const size_t bytes_npix = sizeof(int64_t) * npix.size();
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, bytes_desc + bytes_npix, s);
+  if (e != cudaSuccess) return fail(TDCT_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  PlaneDesc* d_descs = static_cast<PlaneDesc*>(scratch);
+  int64_t* d_npix = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + bytes_desc);
+  if ((e = cudaMemcpyAsync(d_descs, descs.data(), bytes_desc, cudaMemcpyHostToDevice, s)) ==
+          cudaSuccess &&
+      (e = cudaMemcpyAsync(d_npix, npix.data(), bytes_npix, cudaMemcpyHostToDevice, s)) ==
+          cudaSuccess)
+    e = enqueue_batch(groups, d_descs, d_npix, nplanes,
+                      reinterpret_cast<unsigned long long*>(d_sse), d_psnr, s);
+  const cudaError_t ef = cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error_batched");
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  return TDCT_OK;
+}
+
+int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                     const int32_t n[8], int path, tdct_plan** out_plan) {
+  if (!out_plan) return fail(TDCT_EINVAL, "out_plan is NULL");
+  *out_plan = nullptr;
+  int rc = check_transform(T, n);
+  if (rc) return rc;
+  if (path != TDCT_PATH_AUTO && path != TDCT_PATH_BUTTERFLY)
+    return fail(TDCT_EUNSUPPORTED, "path %d is not implemented for batches", path);
+  std::vector<PlaneDesc> descs;
+  std::vector<int64_t> npix;
+  tdct_plan* plan = new (std::nothrow) tdct_plan;
+  if (!plan) return fail(TDCT_ENOMEM, "host allocation failed");
+  if ((rc = build_batch(planes, nplanes, descs, plan->groups, npix))) {
+    delete plan;
+    return rc;
+  }
+  plan->nplanes = nplanes;
+  cudaError_t e = cudaMalloc(&plan->d_descs, sizeof(PlaneDesc) * descs.size());
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_npix, sizeof(int64_t) * npix.size());
+  if (e != cudaSuccess) {
+    tdct_plan_destroy(plan);
+    return fail(TDCT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(plan->d_descs, descs.data(), sizeof(PlaneDesc) * descs.size(),
+                 cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->d_npix, npix.data(), sizeof(int64_t) * npix.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    tdct_plan_destroy(plan);
+    return cuda_fail(e, "tdct_plan_create");
+  }
+  *out_plan = plan;
+  return TDCT_OK;
+}
+
+int tdct_plan_kernel_count(const tdct_plan* plan) {
+  return plan ? (int)plan->groups.size() + 1 : 0;
+}
+
+int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stream_t stream) {
+  if (!plan) return fail(TDCT_EINVAL, "plan is NULL");
+  if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
+    return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
+  std::lock_guard<std::mutex> lock(plan->mu);
+  unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
+  cudaError_t e = cudaSuccess;
+  if (!plan->exec || plan->exec_sse != sse || plan->exec_psnr != d_psnr) {
+    if (plan->exec) {
+      cudaGraphExecDestroy(plan->exec);
+      plan->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    const cudaError_t ee = enqueue_batch(plan->groups, plan->d_descs, plan->d_npix,
+                                         plan->nplanes, sse, d_psnr, plan->capture_stream);
+    e = cudaStreamEndCapture(plan->capture_stream, &graph);
+    if (ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(ee, "plan capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&plan->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      plan->exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    plan->exec_sse = sse;
+    plan->exec_psnr = d_psnr;
+  }
+  e = cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? TDCT_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+void tdct_plan_destroy(tdct_plan* plan) {
+  if (!plan) return;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->capture_stream) cudaStreamDestroy(plan->capture_stream);
+  if (plan->d_descs) cudaFree(plan->d_descs);
+  if (plan->d_npix) cudaFree(plan->d_npix);
+  delete plan;
+}
+
+int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype, int r,
+                         int precision, float* d_coef, void* d_recon, int64_t recon_pitch,
+                         uint64_t* d_sse, double* d_psnr, tdct_stream_t stream) {
+  int rc = check_r(r);
+  if (rc) return rc;
+  if ((rc = check_plane(d_img, pitch, H, W, dtype, "tdct_dct_codec_error"))) return rc;
+  if (d_recon && (rc = check_plane(d_recon, recon_pitch, H, W, dtype, "recon"))) return rc;
+  if (precision != TDCT_FP32 && precision != TDCT_BF16)
+    return fail(TDCT_EINVAL, "precision %d is neither TDCT_FP32 nor TDCT_BF16", precision);
+  if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
+    return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
+  if (d_coef && (reinterpret_cast<uintptr_t>(d_coef) & 3))
+    return fail(TDCT_EINVAL, "d_coef not 4-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
+  cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e, "tdct_dct_codec_error memset");
+  const PlaneDesc P = make_desc(d_img, pitch, H, W, dtype, r, d_recon, recon_pitch, 0);
+  if ((e = launch_dct_codec(P, precision, d_coef, sse, s)) != cudaSuccess)
+    return cuda_fail(e, "tdct_dct_codec_error launch");
+  if (d_psnr) {
+    psnr_kernel<<<1, 32, 0, s>>>(sse, nullptr, (int64_t)H * W, d_psnr, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "psnr launch");
+  }
+  return TDCT_OK;
+}
+
+int tdct_sync_status(tdct_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int status = 0;
+  e = cudaMemcpyFromSymbol(&status, g_status, sizeof status);
+  if (e != cudaSuccess) return cuda_fail(e, "read status word");
+  const int zero = 0;
+  e = cudaMemcpyToSymbol(g_status, &zero, sizeof zero);
+  if (e != cudaSuccess) return cuda_fail(e, "clear status word");
+  if (status == TDCT_ETIMEOUT) return fail(TDCT_ETIMEOUT, "a bounded device wait gave up");
+  if (status != 0) return fail(TDCT_EDEVICE, "device check failed with code %d", status);
+  return TDCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,223 @@
+"""GPU parity of the CUDA library against the CPU oracle (bit-exact).
+
+Every test calls the C ABI through the thin binding on device tensors and
+compares with ``oracle/`` on the same bytes: coefficients, reconstruction
+and SSE must be identical; the exact-DCT path must be within the stated
+tolerances of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1808_02950_gb300 as P
+from oracle import codec as oc
+from oracle import matrices as M
+from paper_1808_02950_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+R_LIST = [1, 2, 3, 4, 5, 6, 8, 9, 10, 15, 16, 17, 21, 28, 31, 32, 33, 36, 45, 50, 55, 63, 64]
+
+
+def rand_plane(rng, H, W, dtype, pitch_extra=0, offset=0):
+    """Random plane as a (possibly strided / offset) view of a larger buffer."""
+    if dtype == np.uint8:
+        host = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    else:
+        host = rng.integers(-255, 256, (H, W)).astype(np.int16)
+    tdt = torch.uint8 if dtype == np.uint8 else torch.int16
+    Wp = W + pitch_extra
+    buf = torch.zeros(H * Wp + offset + 64, dtype=tdt, device=DEV)
+    view = buf[offset: offset + H * Wp].view(H, Wp)[:, :W]
+    view.copy_(torch.from_numpy(host).to(DEV))
+    return host, view
+
+
+def run_codec(view, r, want_recon=True):
+    recon = torch.full_like(view, 77) if want_recon else None
+    sse = torch.zeros(1, dtype=torch.int64, device=DEV)
+    psnr = torch.zeros(1, dtype=torch.float64, device=DEV)
+    P.tdct_codec_error(view, r, sse, recon=recon, psnr=psnr)
+    torch.cuda.synchronize()
+    return int(sse.item()), (recon.cpu().numpy() if recon is not None else None), float(psnr.item())
+
+
+SIZES = [(8, 8), (8, 16), (16, 8), (24, 40), (13, 11), (1, 1), (7, 9), (64, 520), (40, 1032),
+         (9, 1025)]
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+@pytest.mark.parametrize("H,W", SIZES)
+def test_codec_small_planes(H, W, dtype):
+    rng = np.random.default_rng(H * 1000 + W + (7 if dtype == np.int16 else 0))
+    host, view = rand_plane(rng, H, W, dtype)
+    for r in R_LIST[:: 2 if H * W > 4096 else 1]:
+        sse, rec, psnr = run_codec(view, r)
+        want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+        assert np.array_equal(rec, want_rec), f"recon differs at r={r}"
+        assert sse == want_sse
+        assert psnr == pytest.approx(oc.psnr(want_sse, H * W), rel=1e-12) or (
+            want_sse == 0 and psnr == float("inf"))
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+@pytest.mark.parametrize("pitch_extra,offset", [(8, 0), (3, 0), (0, 1), (5, 3), (16, 8)])
+def test_codec_strided_and_unaligned(pitch_extra, offset, dtype):
+    rng = np.random.default_rng(100 + pitch_extra * 10 + offset)
+    host, view = rand_plane(rng, 40, 136, dtype, pitch_extra, offset)
+    for r in (1, 10, 16, 64):
+        sse, rec, _ = run_codec(view, r)
+        want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+        assert np.array_equal(rec, want_rec) and sse == want_sse
+
+
+def test_codec_sse_only():
+    rng = np.random.default_rng(5)
+    host, view = rand_plane(rng, 64, 1040, np.uint8)
+    for r in (3, 16):
+        sse, _, _ = run_codec(view, r, want_recon=False)
+        assert sse == oc.codec_plane(host, M.T1, r, want_recon=False)[0]
+
+
+@pytest.mark.parametrize("r", [1, 4, 10, 16, 32, 64])
+def test_adversarial_blocks(r):
+    blocks = synth.adversarial_blocks(DEV)
+    host = blocks.cpu().numpy()
+    sse, rec, _ = run_codec(blocks, r)
+    want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+    assert np.array_equal(rec, want_rec) and sse == want_sse
+    # the same sign patterns as int16 residuals at +-255
+    res = (blocks.to(torch.int16) * 2 - 255).contiguous()
+    sse, rec, _ = run_codec(res, r)
+    want_sse, want_rec, _ = oc.codec_plane(res.cpu().numpy(), M.T1, r)
+    assert np.array_equal(rec, want_rec) and sse == want_sse
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+def test_forward_cosimulation_100k_vectors(dtype):
+    """100,000 random 8-point vectors through the row and column butterflies
+    (12,500 blocks), as the paper's FPGA co-simulation (§5.2) does."""
+    rng = np.random.default_rng(2112)
+    host, view = rand_plane(rng, 8 * 125, 8 * 100, dtype)
+    coef = torch.zeros((125, 100, 8, 8), dtype=torch.int32, device=DEV)
+    P.tdct_forward(view, coef)
+    torch.cuda.synchronize()
+    _, _, want = oc.codec_plane(host, M.T1, 64, want_recon=False, want_coef=True)
+    assert np.array_equal(coef.cpu().numpy().astype(np.int64), want)
+
+
+@pytest.mark.parametrize("H,W", [(8, 8), (13, 11), (40, 520)])
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+def test_forward_and_zonal_inverse(H, W, dtype):
+    rng = np.random.default_rng(H + W)
+    host, view = rand_plane(rng, H, W, dtype)
+    nby, nbx = (H + 7) // 8, (W + 7) // 8
+    coef = torch.zeros((nby, nbx, 8, 8), dtype=torch.int32, device=DEV)
+    P.tdct_forward(view, coef)
+    out = torch.zeros_like(view)
+    for r in (1, 6, 16, 37, 64):
+        P.tdct_zonal_inverse(coef, r, out)
+        torch.cuda.synchronize()
+        _, want_rec, want_coef = oc.codec_plane(host, M.T1, r, want_coef=True)
+        assert np.array_equal(coef.cpu().numpy().astype(np.int64), want_coef)
+        assert np.array_equal(out.cpu().numpy(), want_rec)
+
+
+def test_single_512_full():
+    """The one-image workload (512x512, rho 0.95, r = 10), bit-exact."""
+    img, r = synth.single_512(DEV)
+    host = img.cpu().numpy()
+    sse, rec, psnr = run_codec(img, r)
+    want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+    assert np.array_equal(rec, want_rec) and sse == want_sse
+    assert psnr == pytest.approx(oc.psnr(want_sse, host.size), rel=1e-12)
+
+
+def _batch(rng):
+    specs = [(64, 64, 4, np.uint8), (72, 136, 8, np.uint8), (13, 11, 16, np.int16),
+             (40, 520, 16, np.uint8), (8, 8, 64, np.int16), (33, 65, 32, np.uint8),
+             (16, 1032, 4, np.int16), (24, 24, 16, np.uint8)]
+    hosts, views, recons, rs = [], [], [], []
+    for H, W, r, dt in specs:
+        h, v = rand_plane(rng, H, W, dt)
+        hosts.append(h)
+        views.append(v)
+        recons.append(torch.zeros_like(v))
+        rs.append(r)
+    return hosts, views, recons, rs
+
+
+def test_batched_matches_oracle():
+    rng = np.random.default_rng(77)
+    hosts, views, recons, rs = _batch(rng)
+    planes = P.make_planes(views, rs, recons)
+    sse = torch.zeros(len(views), dtype=torch.int64, device=DEV)
+    psnr = torch.zeros(len(views), dtype=torch.float64, device=DEV)
+    P.tdct_codec_error_batched(planes, sse, psnr)
+    torch.cuda.synchronize()
+    for i, h in enumerate(hosts):
+        want_sse, want_rec, _ = oc.codec_plane(h, M.T1, rs[i])
+        assert int(sse[i]) == want_sse
+        assert np.array_equal(recons[i].cpu().numpy(), want_rec)
+        assert float(psnr[i]) == pytest.approx(oc.psnr(want_sse, h.size), rel=1e-12)
+
+
+def test_plan_graph_replay():
+    rng = np.random.default_rng(78)
+    hosts, views, recons, rs = _batch(rng)
+    planes = P.make_planes(views, rs, recons)
+    plan = P.tdct_plan_create(planes)
+    assert plan.kernel_count() >= 2
+    want = [oc.codec_plane(h, M.T1, rs[i])[0] for i, h in enumerate(hosts)]
+    for rep in range(3):
+        sse = torch.full((len(views),), -1, dtype=torch.int64, device=DEV)
+        plan.launch(sse)
+        torch.cuda.synchronize()
+        assert [int(v) for v in sse.cpu()] == want
+    plan.close()
+
+
+def _dct_rel_err(got, want):
+    """Per plane: max |Y_gpu - Y_64| / max |Y_64| (a zero denominator counts as 1)."""
+    den = np.abs(want).max()
+    return np.abs(got - want).max() / (den if den > 0 else 1.0)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+def test_dct_fp32_within_tolerance(dtype):
+    rng = np.random.default_rng(300)
+    host, view = rand_plane(rng, 64, 136, dtype)
+    img, _ = synth.single_512(DEV)
+    for h, v in ((host, view), (img.cpu().numpy(), img)):
+        Hh, Ww = h.shape
+        coef = torch.zeros(((Hh + 7) // 8, (Ww + 7) // 8, 8, 8), dtype=torch.float32, device=DEV)
+        for r in (1, 10, 16, 64):
+            sse = torch.zeros(1, dtype=torch.int64, device=DEV)
+            psnr = torch.zeros(1, dtype=torch.float64, device=DEV)
+            P.tdct_dct_codec_error(v, r, sse, precision=P.TDCT_FP32, coef=coef, psnr=psnr)
+            torch.cuda.synchronize()
+            want_sse, _, want_coef = oc.dct_codec_plane(h, r, want_recon=False, want_coef=True)
+            assert _dct_rel_err(coef.cpu().numpy().astype(np.float64), want_coef) <= 1e-5
+            p64 = oc.psnr(want_sse, h.size)
+            if np.isfinite(p64):
+                assert abs(float(psnr.item()) - p64) <= 0.01
+            else:
+                assert int(sse.item()) <= 2  # r = 64: only rounding ties can differ
+
+
+def test_dct_bf16_error_is_bounded():
+    img, _ = synth.single_512(DEV)
+    h = img.cpu().numpy()
+    coef = torch.zeros((64, 64, 8, 8), dtype=torch.float32, device=DEV)
+    sse = torch.zeros(1, dtype=torch.int64, device=DEV)
+    P.tdct_dct_codec_error(img, 16, sse, precision=P.TDCT_BF16, coef=coef)
+    torch.cuda.synchronize()
+    want_sse, _, want_coef = oc.dct_codec_plane(h, 16, want_recon=False, want_coef=True)
+    err = _dct_rel_err(coef.cpu().numpy().astype(np.float64), want_coef)
+    # bf16 carries 8 significant bits: two rounded stages stay within a few 2^-8
+    assert err <= 2.0**-6
+    assert abs(oc.psnr(int(sse.item()), h.size) - oc.psnr(want_sse, h.size)) <= 0.5
+
+
+def test_status_word_clean():
+    P.tdct_sync_status()
