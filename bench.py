@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch_1024x1024",
                     choices=["batch_1024x1024", "ragged_2000", "video_600x1080p", "single_512"])
+    ap.add_argument("--images", type=int, default=1024,
+                    help="images of batch_1024x1024 (smaller only for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -164,7 +166,7 @@ def measured_peaks():
 class Workload:
     """Planes of one workload resident on the GPU, with reconstruction buffers."""
 
-    def __init__(self, name: str, device: str):
+    def __init__(self, name: str, device: str, images: int = 1024):
         import torch
 
         from paper_1808_02950_gb300 import synth
@@ -172,7 +174,7 @@ class Workload:
         self.name = name
         self.planes = []  # (img tensor 2-D, r)
         if name == "batch_1024x1024":
-            imgs, r = synth.batch_1024x1024(device)
+            imgs, r = synth.batch_1024x1024(device, n=images)
             self.storage = [imgs]
             self.planes = [(imgs[i], r) for i in range(imgs.shape[0])]
             self.desc = {"workload": "batch_1024x1024", "images": int(imgs.shape[0]),
@@ -213,7 +215,7 @@ def time_ours(args, dist, out):
 
     dev = f"cuda:{dist.local_rank}"
     torch.cuda.set_device(dev)
-    wl = Workload(args.workload, dev)
+    wl = Workload(args.workload, dev, args.images)
     planes = P.make_planes([p for p, _ in wl.planes], [r for _, r in wl.planes], wl.recons)
     n = len(wl.planes)
     sse = torch.zeros(n, dtype=torch.int64, device=dev)
@@ -378,7 +380,7 @@ def main_reference(args):
 
     oc.lib()
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    wl = Workload(args.workload, dev)
+    wl = Workload(args.workload, dev, args.images)
     sample = host_sample(wl, 64)
     per_step_budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):

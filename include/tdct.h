@@ -168,6 +168,17 @@ int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dty
  */
 int tdct_sync_status(tdct_stream_t stream);
 
+/*
+ * Test hook for the bounded waits (no counterpart in the paper).  With
+ * enable != 0, the next fused-codec launch that uses the bulk-copy ring
+ * withholds one copy, so its mbarrier wait gives up after about 10 ms and
+ * records TDCT_ETIMEOUT in the status word instead of waiting for ever; the
+ * launch's results are then incomplete.  The hook disarms itself after one
+ * launch.  Used by the test suite to check that a stuck copy is reported and
+ * leaves the context usable.
+ */
+int tdct_debug_inject_wait_timeout(int enable);
+
 /* Thread-local description of the last error returned on this thread. */
 const char* tdct_last_error(void);
 

@@ -34,7 +34,8 @@ N1 = (8, 18, 20, 18, 8, 18, 20, 18)
 EXPORTS = (
     "tdct_forward", "tdct_zonal_inverse", "tdct_codec_error", "tdct_codec_error_batched",
     "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_destroy",
-    "tdct_dct_codec_error", "tdct_sync_status", "tdct_last_error", "tdct_version",
+    "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
+    "tdct_last_error", "tdct_version",
 )
 
 
@@ -81,6 +82,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_plan_destroy.restype = None
     L.tdct_dct_codec_error.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp, vp, i64, vp, vp, vp]
     L.tdct_sync_status.argtypes = [vp]
+    L.tdct_debug_inject_wait_timeout.argtypes = [i32]
     L.tdct_last_error.restype = ctypes.c_char_p
     L.tdct_version.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -232,6 +234,10 @@ def tdct_dct_codec_error(img, r: int, sse, precision=TDCT_FP32, coef=None, recon
     _check(load().tdct_dct_codec_error(_ptr(img), pitch, H, W, dt, int(r), int(precision),
                                        _ptr(coef), _ptr(recon), rp, _ptr(sse), _ptr(psnr),
                                        _stream(stream)))
+
+
+def tdct_debug_inject_wait_timeout(enable: bool = True) -> None:
+    _check(load().tdct_debug_inject_wait_timeout(1 if enable else 0))
 
 
 def tdct_sync_status(stream=None) -> None:

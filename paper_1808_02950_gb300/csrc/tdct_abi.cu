@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -15,6 +16,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -99,10 +101,31 @@ int check_r(int r) {
   return TDCT_OK;
 }
 
+// One-shot test hook: the next codec launch withholds one bulk copy so that
+// its bounded wait runs out (see tdct_debug_inject_wait_timeout).
+std::atomic<int> g_inject_timeout{0};
+
+int* status_word() {
+  static void* addr[256] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev] && cudaGetSymbolAddress(&addr[dev], g_status) != cudaSuccess) addr[dev] = nullptr;
+  return static_cast<int*>(addr[dev]);
+}
+
 CodecParams make_params(int r) {
   CodecParams cp;
+  std::memset(&cp, 0, sizeof cp);
   for (int i = 0; i < 8; ++i)
     for (int j = 0; j < 8; ++j) cp.cmul[8 * i + j] = kept(r, i, j) ? q_of(i) * q_of(j) : 0;
+  cp.status = status_word();
+  cp.wait_limit = 2000000000ll;  // about a second of SM clock
+  if (g_inject_timeout.exchange(0)) {
+    cp.test_hook = 1;
+    cp.wait_limit = 20000000ll;
+  }
   return cp;
 }
 
@@ -125,7 +148,10 @@ PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int
   d.chunks = (d.nbx + 63) / 64;
   d.dtype = dtype;
   d.r = r;
-  d.vec16 = (aligned8(img, pitch) ? 1 : 0) | ((recon && aligned8(recon, recon_pitch)) ? 2 : 0);
+  const bool bulk = dtype == TDCT_U8 && ((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch) & 15) == 0 &&
+                    W % 16 == 0 && H % 8 == 0 && (!recon || aligned8(recon, recon_pitch));
+  d.vec16 = (aligned8(img, pitch) ? 1 : 0) | ((recon && aligned8(recon, recon_pitch)) ? 2 : 0) |
+            (bulk ? 4 : 0);
   d.slot = slot;
   return d;
 }
@@ -239,13 +265,14 @@ struct Group {
   int dtype, r;
   int first, count;
   int64_t units;
+  int any_bulk;
 };
 
 int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& descs,
                 std::vector<Group>& groups, std::vector<int64_t>& npix) {
   if (!planes || nplanes < 1 || nplanes > (1 << 20))
     return fail(TDCT_EINVAL, "nplanes = %d outside 1..2^20 (or planes is NULL)", nplanes);
-  std::map<std::pair<int, int>, std::vector<int>> by_key;
+  std::map<std::tuple<int, int, int>, std::vector<int>> by_key;
   npix.resize(nplanes);
   for (int i = 0; i < nplanes; ++i) {
     const tdct_plane& p = planes[i];
@@ -256,13 +283,15 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
     if (p.r < 1 || p.r > 64) return fail(TDCT_EINVAL, "plane %d: r = %d outside 1..64", i, p.r);
     if (p.recon && p.recon_pitch < (int64_t)p.W * sample_bytes(p.dtype))
       return fail(TDCT_EINVAL, "plane %d: recon pitch too small", i);
-    by_key[{p.dtype, p.r}].push_back(i);
+    const PlaneDesc probe = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, p.r, p.recon, p.recon_pitch, i);
+    by_key[{p.dtype, p.r, (probe.vec16 & 4) ? 1 : 0}].push_back(i);
     npix[i] = (int64_t)p.H * p.W;
   }
   descs.clear();
   groups.clear();
   for (auto& kv : by_key) {
-    Group g{kv.first.first, kv.first.second, (int)descs.size(), (int)kv.second.size(), 0};
+    Group g{std::get<0>(kv.first), std::get<1>(kv.first), (int)descs.size(),
+            (int)kv.second.size(), 0, std::get<2>(kv.first)};
     for (int i : kv.second) {
       const tdct_plane& p = planes[i];
       PlaneDesc d = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, p.r, p.recon, p.recon_pitch, i);
@@ -287,6 +316,7 @@ cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_d
     tab.d = d_descs + g.first;
     tab.n = g.count;
     tab.total_units = g.units;
+    tab.any_bulk = g.any_bulk;
     if ((e = dispatch_codec(g.r, g.dtype, tab, sse, 0, s)) != cudaSuccess) return e;
   }
   if (psnr) {
@@ -378,6 +408,7 @@ int tdct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype,
   tab.n = 1;
   tab.one = make_desc(d_img, pitch, H, W, dtype, r, d_recon, recon_pitch, 0);
   tab.total_units = units_of(tab.one);
+  tab.any_bulk = (tab.one.vec16 & 4) ? 1 : 0;
   unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error memset");
@@ -534,6 +565,11 @@ int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dty
     psnr_kernel<<<1, 32, 0, s>>>(sse, nullptr, (int64_t)H * W, d_psnr, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "psnr launch");
   }
+  return TDCT_OK;
+}
+
+int tdct_debug_inject_wait_timeout(int enable) {
+  g_inject_timeout.store(enable ? 1 : 0);
   return TDCT_OK;
 }
 

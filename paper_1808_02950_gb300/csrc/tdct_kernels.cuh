@@ -30,7 +30,8 @@ struct PlaneDesc {
   int32_t chunks;      // units per block-row = ceil(nbx / 64)
   int32_t dtype;       // 0 = u8, 1 = i16
   int32_t r;
-  int32_t vec16;       // bit 0: img rows 8-byte aligned; bit 1: recon rows
+  int32_t vec16;       // bit 0: img rows 8-byte aligned; bit 1: recon rows;
+                       // bit 2: u8 plane eligible for the bulk-copy ring
   int32_t slot;        // output index for SSE / PSNR
   int32_t pad_;
 };
@@ -38,7 +39,7 @@ struct PlaneDesc {
 struct PlaneTable {
   const PlaneDesc* d;  // device array, or nullptr to use `one`
   int32_t n;
-  int32_t pad_;
+  int32_t any_bulk;    // some plane takes the bulk-copy path (vec16 bit 2)
   int64_t total_units;
   PlaneDesc one;
 };
@@ -150,6 +151,10 @@ __device__ __forceinline__ void reconstruct(uint32_t w[64], int32_t out[64]) {
 // in, §6.1).  Lives in the kernel parameter (constant) bank.
 struct CodecParams {
   int32_t cmul[64];
+  int* status;           // device status word (TDCT_ETIMEOUT on a bounded wait giving up)
+  long long wait_limit;  // clock cycles a bulk-copy wait may take before giving up
+  int32_t test_hook;     // 1: the first copy of warp 0 is never issued (timeout test)
+  int32_t pad_;
 };
 
 // Forward, zonal mask, scale by q_i q_j, inverse, round and clamp one block.
@@ -319,9 +324,215 @@ __device__ __forceinline__ uint32_t codec_lane(const PlaneDesc& P, int by, int b
   return sse;
 }
 
+// ---- u8 fast path: two blocks per 32-bit register ------------------------------
+//
+// The forward transform of the two blocks of a lane runs on packed registers
+// v = a + 65536 b (mod 2^32), a from block A, b from block B.  Additions,
+// subtractions and doublings act on both lanes at once and are exact modulo
+// 2^32; each lane is recovered exactly as long as its final value lies in
+// [-32768, 32767].  For u8 samples |Z_ij| <= 144 * 127.5 for (i, j) != (0, 0)
+// and 0 <= Z_00 <= 16320, so every coefficient fits (intermediates may wrap).
+//
+// The inverse is per block in int32 and is streamed row by row into the
+// epilogue.  With doubled multipliers the inverse yields 2N + L^2, and
+// mulhi(2N + L^2, kDivMagic) carries x' = floor((N + L^2/2) / L^2) in its high
+// 16 bits; one prmt packs two of them as s16x2, one min.relu.s16x2 clamps
+// both to [0, 255], one prmt packs four bytes.  SSE per block is
+// sum x^2 + sum x'^2 - 2 sum x x' from byte dot products (dp4a), exact in
+// uint32 arithmetic since the true value is below 2^32.
+
+__device__ __forceinline__ uint32_t min_relu_s16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.relu.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Lanes (block A, block B) of the 8 samples of one row pair.
+__device__ __forceinline__ void pair_row(uint2 a, uint2 b, uint32_t p[8]) {
+  const uint32_t a02 = __byte_perm(a.x, 0u, 0x4240u), a13 = __byte_perm(a.x, 0u, 0x4341u);
+  const uint32_t b02 = __byte_perm(b.x, 0u, 0x4240u), b13 = __byte_perm(b.x, 0u, 0x4341u);
+  const uint32_t a46 = __byte_perm(a.y, 0u, 0x4240u), a57 = __byte_perm(a.y, 0u, 0x4341u);
+  const uint32_t b46 = __byte_perm(b.y, 0u, 0x4240u), b57 = __byte_perm(b.y, 0u, 0x4341u);
+  p[0] = __byte_perm(a02, b02, 0x5410u);
+  p[2] = __byte_perm(a02, b02, 0x7632u);
+  p[1] = __byte_perm(a13, b13, 0x5410u);
+  p[3] = __byte_perm(a13, b13, 0x7632u);
+  p[4] = __byte_perm(a46, b46, 0x5410u);
+  p[6] = __byte_perm(a46, b46, 0x7632u);
+  p[5] = __byte_perm(a57, b57, 0x5410u);
+  p[7] = __byte_perm(a57, b57, 0x7632u);
+}
+
+__device__ __forceinline__ int32_t lane_lo(uint32_t v) { return (int32_t)(int16_t)(v & 0xffffu); }
+__device__ __forceinline__ int32_t lane_hi(uint32_t v) {
+  return (int32_t)(v - (uint32_t)lane_lo(v)) >> 16;
+}
+
+// Round, clamp and pack one row of 8 doubled-and-biased inverse values.
+__device__ __forceinline__ uint2 round_pack_row_u8(const uint32_t n2[8]) {
+  uint32_t h[8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) h[l] = (uint32_t)__mulhi((int32_t)n2[l], kDivMagic);
+  const uint32_t c01 = min_relu_s16x2(__byte_perm(h[0], h[1], 0x7632u), 0x00ff00ffu);
+  const uint32_t c23 = min_relu_s16x2(__byte_perm(h[2], h[3], 0x7632u), 0x00ff00ffu);
+  const uint32_t c45 = min_relu_s16x2(__byte_perm(h[4], h[5], 0x7632u), 0x00ff00ffu);
+  const uint32_t c67 = min_relu_s16x2(__byte_perm(h[6], h[7], 0x7632u), 0x00ff00ffu);
+  return make_uint2(__byte_perm(c01, c23, 0x6420u), __byte_perm(c45, c67, 0x6420u));
+}
+
+// Inverse of one block from its kept, scaled coefficients w (doubled and
+// biased), streamed by rows into rounding, SSE terms and the store.
+// `valid_cols` = samples of each row inside the plane (8 when full),
+// `valid_rows` = rows inside the plane.  Returns sum x^2 + x'^2 - 2 x x'.
+template <int R>
+__device__ __forceinline__ uint32_t inverse_epilogue_u8(const uint32_t w[64], const uint2 x[8],
+                                                        uint2* __restrict__ out_row0,
+                                                        int64_t out_pitch, bool store,
+                                                        bool full, int valid_rows,
+                                                        int valid_cols) {
+  // columns first: v[k][j] = sum_i t_i[k] w[i][j] (only columns with kept entries)
+  uint32_t v[64];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    uint32_t col[8], o[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) col[i] = w[8 * i + j];
+    inv8<uint32_t>(col, o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[8 * k + j] = o[k];
+  }
+  uint32_t acc = 0;
+  const uint64_t colmask =
+      valid_cols >= 8 ? ~0ull : ((1ull << (8 * valid_cols)) - 1ull);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    uint32_t n2[8];
+    inv8<uint32_t>(v + 8 * k, n2);
+    uint2 y = round_pack_row_u8(n2);
+    if (!full) {
+      const uint64_t m = k < valid_rows ? colmask : 0ull;
+      y.x &= (uint32_t)m;
+      y.y &= (uint32_t)(m >> 32);
+    }
+    acc = __dp4a(y.x, y.x, acc);
+    acc = __dp4a(y.y, y.y, acc);
+    acc -= 2u * __dp4a(x[k].x, y.x, __dp4a(x[k].y, y.y, 0u));
+    if (store && full) out_row0[(int64_t)k * (out_pitch >> 3)] = y;
+    if (store && !full && k < valid_rows) {
+      uint8_t* row = reinterpret_cast<uint8_t*>(out_row0) + (int64_t)k * out_pitch;
+#pragma unroll
+      for (int l = 0; l < 8; ++l)
+        if (l < valid_cols) row[l] = (uint8_t)((l < 4 ? y.x >> (8 * l) : y.y >> (8 * (l - 4))) & 0xffu);
+    }
+  }
+  return acc;
+}
+
+// Both blocks of a lane (samples already in registers, zero outside the
+// plane) through the packed forward and the per-block inverse.
+// FULL: the caller guarantees both blocks exist, lie inside the plane and
+// that recon (if any) has 8-byte aligned rows (the bulk-copy planes).
+template <int R, bool FULL = false>
+__device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, int bx0,
+                                                  const uint2 xa[8], const uint2 xb[8],
+                                                  const CodecParams& cp) {
+  const bool has0 = FULL || bx0 < P.nbx, has1 = FULL || bx0 + 1 < P.nbx;
+  if (!has0) return 0u;
+  const int valid_rows = FULL ? 8 : min(8, P.H - by * 8);
+  const int vc0 = FULL ? 8 : min(8, P.W - bx0 * 8), vc1 = FULL ? 8 : min(8, P.W - (bx0 + 1) * 8);
+  const bool full0 = FULL || (valid_rows == 8 && vc0 == 8);
+  const bool full1 = FULL || (has1 && valid_rows == 8 && vc1 == 8);
+  uint32_t sse = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    sse = __dp4a(xa[k].x, xa[k].x, sse);
+    sse = __dp4a(xa[k].y, xa[k].y, sse);
+    sse = __dp4a(xb[k].x, xb[k].x, sse);
+    sse = __dp4a(xb[k].y, xb[k].y, sse);
+  }
+  // packed forward: rows, then columns
+  uint32_t z[64];
+  {
+    uint32_t t[64];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      uint32_t p[8];
+      pair_row(xa[k], xb[k], p);
+      fwd8<uint32_t>(p, t + 8 * k);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      uint32_t col[8], o[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) col[k] = t[8 * k + j];
+      fwd8<uint32_t>(col, o);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) z[8 * i + j] = o[i];
+    }
+  }
+  const bool store = P.recon != nullptr;
+  const int64_t rp = P.recon_pitch;
+  uint2* out0 = store ? reinterpret_cast<uint2*>(P.recon + (int64_t)(by * 8) * rp + (int64_t)bx0 * 8)
+                      : nullptr;
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    if (b == 1 && !has1) break;
+    uint32_t w[64];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int p = 8 * i + j;
+        if (kept(R, i, j)) {
+          const int32_t zz = b == 0 ? lane_lo(z[p]) : lane_hi(z[p]);
+          w[p] = (uint32_t)zz * (uint32_t)(2 * cp.cmul[p]);
+        } else {
+          w[p] = 0u;
+        }
+      }
+    w[0] += kL2;  // doubled bias: 2 (N + L^2/2)
+    const bool full = b == 0 ? full0 : full1;
+    const bool fast_store = store && full && (FULL || (P.vec16 & 2));
+    uint2* o = store ? (b == 0 ? out0 : out0 + 1) : nullptr;
+    if (!FULL && store && !fast_store) {
+      // unaligned recon or edge block: byte stores of valid samples
+      sse += inverse_epilogue_u8<R>(w, b == 0 ? xa : xb, o, rp, true, false, valid_rows,
+                                    b == 0 ? vc0 : vc1);
+    } else {
+      sse += inverse_epilogue_u8<R>(w, b == 0 ? xa : xb, o, rp, store, full, valid_rows,
+                                    b == 0 ? vc0 : vc1);
+    }
+  }
+  return sse;
+}
+
+// Load both blocks of a lane with plain global loads, then run the codec.
+template <int R>
+__device__ __forceinline__ uint32_t codec_lane_u8(const PlaneDesc& P, int by, int bx0,
+                                                  const CodecParams& cp) {
+  const bool has0 = bx0 < P.nbx, has1 = bx0 + 1 < P.nbx;
+  if (!has0) return 0u;
+  const bool rows_in = by * 8 + 8 <= P.H;
+  const bool full0 = rows_in && (bx0 + 1) * 8 <= P.W, full1 = has1 && rows_in && (bx0 + 2) * 8 <= P.W;
+  RowWords<0> ra, rb;
+  load_block<0>(P, by, bx0, full0 && (P.vec16 & 1), ra);
+  if (has1) load_block<0>(P, by, bx0 + 1, full1 && (P.vec16 & 1), rb);
+  else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) rb.w[k] = make_uint2(0u, 0u);
+  }
+  return codec_pair_u8<R>(P, by, bx0, ra.w, rb.w, cp);
+}
+
 // Persistent fused codec: every warp takes a contiguous range of units.
+// Resident CTAs per SM the u8 kernel is compiled for (registers <= 65536 /
+// (256 * TDCT_U8_MINB)); the int16 kernel keeps one.
+#ifndef TDCT_U8_MINB
+#define TDCT_U8_MINB 2
+#endif
+
 template <int R, int DT>
-__global__ void __launch_bounds__(256) codec_kernel(const PlaneTable tab, const CodecParams cp,
+__global__ void __launch_bounds__(256, DT == 0 ? TDCT_U8_MINB : 1) codec_kernel(const PlaneTable tab, const CodecParams cp,
                                                     unsigned long long* __restrict__ sse_out) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -348,7 +559,8 @@ __global__ void __launch_bounds__(256) codec_kernel(const PlaneTable tab, const 
     const int64_t local = u - P.unit_begin;
     const int by = (int)(local / P.chunks);
     const int chunk = (int)(local - (int64_t)by * P.chunks);
-    acc += codec_lane<R, DT>(P, by, chunk * 64 + 2 * lane, cp);
+    if constexpr (DT == 0) acc += codec_lane_u8<R>(P, by, chunk * 64 + 2 * lane, cp);
+    else acc += codec_lane<R, DT>(P, by, chunk * 64 + 2 * lane, cp);
   }
   if (p >= 0) {
     acc = warp_sum_u64(acc);
@@ -356,29 +568,234 @@ __global__ void __launch_bounds__(256) codec_kernel(const PlaneTable tab, const 
   }
 }
 
+// ---- u8 path with a bulk-copy ring in shared memory -------------------------
+//
+// Each warp owns STAGES slots of 8 rows x 512 bytes (one unit) in shared
+// memory and one mbarrier per slot.  While it computes unit u, the copies of
+// its next STAGES - 1 units are in flight: lane k < 8 issues the 1-D bulk
+// copy (cp.async.bulk, the TMA engine) of row k of the unit, lane 0 arms the
+// slot's mbarrier with the byte count.  The waits are bounded: a wait that
+// gives up records TDCT_ETIMEOUT in the status word, drains the warp's other
+// copies (again bounded) and ends the warp, so a stuck copy never hangs the
+// GPU.  Planes whose rows are not 16-byte aligned, whose width is not a
+// multiple of 16 or whose height is not a multiple of 8 take the plain-load
+// path (codec_kernel); the host never puts them in a ring launch.  Ring
+// planes have H % 8 == 0 and W % 16 == 0, so every existing block is full
+// and both blocks of a lane exist together.
+constexpr int kUnitBytes = 8 * 512;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(bar),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`; false if `limit` cycles pass first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+
+template <int R, int STAGES>
+__global__ void __launch_bounds__(256, TDCT_U8_MINB)
+    codec_u8_tma_kernel(const PlaneTable tab, const CodecParams cp,
+                        unsigned long long* __restrict__ sse_out) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t* ring = smem + (size_t)wid * STAGES * kUnitBytes;
+  const uint32_t bars = smem_addr(smem + (size_t)(blockDim.x >> 5) * STAGES * kUnitBytes) +
+                        (uint32_t)(wid * STAGES * 8);
+  if (lane == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) mbar_init(bars + 8 * s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t U = tab.total_units;
+  const int64_t u_begin = (U * warp) / nwarps;
+  const int64_t u_end = (U * (warp + 1)) / nwarps;
+
+  // producer cursor: the fields of the plane of the next unit to prefetch
+  int64_t pp_end = -1, pp_ubegin = 0, pp_pitch = 0;
+  const uint8_t* pp_img = nullptr;
+  int pp_W = 0, pp_chunks = 1;
+  uint32_t issued = 0;  // bit s: slot s holds a copy in flight
+  uint32_t phase = 0;   // bit s: parity of slot s's next completion
+  int64_t u_pf = u_begin;
+
+  auto issue_next = [&]() {
+    const int64_t u = u_pf++;
+    const int s = (int)((u - u_begin) % STAGES);
+    if (u >= pp_end) {
+      const int q = find_plane(tab, u);
+      const PlaneDesc& Q = tab.d ? tab.d[q] : tab.one;
+      pp_img = Q.img;
+      pp_pitch = Q.pitch;
+      pp_W = Q.W;
+      pp_chunks = Q.chunks;
+      pp_ubegin = Q.unit_begin;
+      pp_end = (q + 1 < tab.n) ? tab.d[q + 1].unit_begin : U;
+    }
+    const int64_t local = u - pp_ubegin;
+    const int by = (int)(local / pp_chunks);
+    const int chunk = (int)(local - (int64_t)by * pp_chunks);
+    const uint32_t row_bytes = (uint32_t)min(512, pp_W - chunk * 512);
+    const uint32_t bar = bars + 8 * s;
+    // order this warp's earlier generic reads of the slot before the async writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (lane == 0) mbar_arrive_expect_tx(bar, 8u * row_bytes);
+    __syncwarp();
+    const bool skip = cp.test_hook == 1 && warp == 0 && u == u_begin;
+    if (lane < 8 && !skip) {
+      const uint8_t* src = pp_img + (int64_t)(by * 8 + lane) * pp_pitch + (int64_t)chunk * 512;
+      bulk_copy_g2s(smem_addr(ring + s * kUnitBytes + lane * 512), src, row_bytes, bar);
+    }
+    issued |= 1u << s;
+  };
+
+  // Bounded wait for slot s; on failure record the timeout, drain the other
+  // slots (bounded) and report false.
+  auto wait_slot = [&](int s) -> bool {
+    const bool ok = __all_sync(0xffffffffu,
+                               mbar_wait_bounded(bars + 8 * s, (phase >> s) & 1u, cp.wait_limit));
+    if (ok) {
+      phase ^= 1u << s;
+      issued &= ~(1u << s);
+      return true;
+    }
+    if (lane == 0 && cp.status) atomicExch(cp.status, 4 /* TDCT_ETIMEOUT */);
+    for (int o = 0; o < STAGES; ++o)
+      if (o != s && (issued >> o & 1u)) mbar_wait_bounded(bars + 8 * o, (phase >> o) & 1u, cp.wait_limit);
+    return false;
+  };
+
+  for (int k = 0; k < STAGES && u_pf < u_end; ++k) issue_next();
+
+  int p = -1;
+  int64_t p_end = -1;
+  PlaneDesc P;
+  unsigned long long acc = 0;
+  for (int64_t u = u_begin; u < u_end; ++u) {
+    if (u >= p_end) {
+      if (p >= 0) {
+        acc = warp_sum_u64(acc);
+        if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+        acc = 0;
+      }
+      p = find_plane(tab, u);
+      P = tab.d ? tab.d[p] : tab.one;
+      p_end = (p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U;
+    }
+    const int64_t local = u - P.unit_begin;
+    const int by = (int)(local / P.chunks);
+    const int chunk = (int)(local - (int64_t)by * P.chunks);
+    const int bx0 = chunk * 64 + 2 * lane;
+    const int s = (int)((u - u_begin) % STAGES);
+    if (!wait_slot(s)) return;
+    uint2 xa[8], xb[8];
+    const uint8_t* slot = ring + s * kUnitBytes + lane * 16;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint4 v = *reinterpret_cast<const uint4*>(slot + k * 512);
+      xa[k] = make_uint2(v.x, v.y);
+      xb[k] = make_uint2(v.z, v.w);
+    }
+    __syncwarp();
+    if (u_pf < u_end) issue_next();  // refill the slot just read
+    if (bx0 < P.nbx) acc += codec_pair_u8<R, true>(P, by, bx0, xa, xb, cp);
+  }
+  if (p >= 0) {
+    acc = warp_sum_u64(acc);
+    if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+  }
+}
+
+// Slots per warp of the bulk-copy ring (2 CTAs x 8 warps x 3 x 4 KB fit 228 KB).
+#ifndef TDCT_U8_STAGES
+#define TDCT_U8_STAGES 3
+#endif
+
+inline int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
+}
+
 // Host-side launcher of one instantiation (defined where instantiated).
+// `max_ctas` > 0 caps the persistent grid (autotuning, tests).
 template <int R, int DT>
 cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned long long* sse,
                          int max_ctas, cudaStream_t s) {
   constexpr int kThreads = 256;
-  static int resident = 0;  // CTAs per SM, computed once per instantiation
+  constexpr int kStages = TDCT_U8_STAGES;
+  constexpr size_t kSmem = (size_t)(kThreads / 32) * kStages * (kUnitBytes + 8);
+  static int resident = 0, resident_bulk = 0;  // CTAs per SM, computed once
   static int sms = 0;
   if (resident == 0) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, codec_kernel<R, DT>, kThreads, 0);
+    sms = device_sms();
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, codec_kernel<R, DT>, kThreads, 0);
     if (e != cudaSuccess) return e;
     if (resident < 1) resident = 1;
+    if constexpr (DT == 0) {
+      e = cudaFuncSetAttribute(codec_u8_tma_kernel<R, kStages>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &resident_bulk, codec_u8_tma_kernel<R, kStages>, kThreads, kSmem);
+      if (e != cudaSuccess) return e;
+      if (resident_bulk < 1) resident_bulk = 1;
+    }
   }
-  const int64_t warps_needed = tab.total_units;
-  int64_t grid = (int64_t)resident * sms;
-  const int64_t by_work = (warps_needed + kThreads / 32 - 1) / (kThreads / 32);
+  const bool bulk = DT == 0 && tab.any_bulk;
+  int64_t grid = (int64_t)(bulk ? resident_bulk : resident) * sms;
+  const int64_t by_work = (tab.total_units + kThreads / 32 - 1) / (kThreads / 32);
   if (by_work < grid) grid = by_work;
   if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   if (grid < 1) grid = 1;
+  if constexpr (DT == 0) {
+    if (bulk) {
+      codec_u8_tma_kernel<R, kStages><<<(unsigned)grid, kThreads, kSmem, s>>>(tab, cp, sse);
+      return cudaGetLastError();
+    }
+  }
   codec_kernel<R, DT><<<(unsigned)grid, kThreads, 0, s>>>(tab, cp, sse);
   return cudaGetLastError();
 }

@@ -221,3 +221,54 @@ def test_dct_bf16_error_is_bounded():
 
 def test_status_word_clean():
     P.tdct_sync_status()
+
+
+@pytest.mark.parametrize("H,W", [(8, 16), (16, 512), (64, 1040), (48, 2048), (8, 4096)])
+def test_bulk_copy_ring_planes(H, W):
+    """u8 planes with 16-byte aligned rows, W % 16 == 0 and H % 8 == 0 take the
+    bulk-copy ring (including a ragged last unit when W is not a multiple of 512)."""
+    rng = np.random.default_rng(H * 7 + W)
+    host = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    img = torch.from_numpy(host).to(DEV)
+    for r in (1, 10, 16, 40, 64):
+        sse, rec, _ = run_codec(img, r)
+        want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+        assert np.array_equal(rec, want_rec) and sse == want_sse
+        sse2, _, _ = run_codec(img, r, want_recon=False)
+        assert sse2 == want_sse
+
+
+def test_bulk_copy_ring_many_units_per_warp():
+    """Enough units that every warp walks its ring many times, across planes."""
+    imgs, _ = synth.batch_1024x1024(DEV, n=48)
+    r = 16
+    recons = torch.empty_like(imgs)
+    planes = P.make_planes([imgs[i] for i in range(48)], [r] * 48, [recons[i] for i in range(48)])
+    sse = torch.zeros(48, dtype=torch.int64, device=DEV)
+    P.tdct_codec_error_batched(planes, sse)
+    torch.cuda.synchronize()
+    for i in (0, 1, 23, 47):
+        want_sse, want_rec, _ = oc.codec_plane(imgs[i].cpu().numpy(), M.T1, r)
+        assert int(sse[i]) == want_sse
+        assert np.array_equal(recons[i].cpu().numpy(), want_rec)
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives():
+    """A withheld bulk copy makes one warp's bounded wait give up: the library
+    reports TDCT_ETIMEOUT through the status word, nothing hangs, and the
+    next call is correct."""
+    rng = np.random.default_rng(9)
+    host = rng.integers(0, 256, (64, 1024)).astype(np.uint8)
+    img = torch.from_numpy(host).to(DEV)
+    P.tdct_sync_status()  # clean start
+    P.tdct_debug_inject_wait_timeout(True)
+    sse = torch.zeros(1, dtype=torch.int64, device=DEV)
+    P.tdct_codec_error(img, 16, sse)
+    with pytest.raises(P.TdctError) as e:
+        P.tdct_sync_status()
+    assert e.value.code == 4  # TDCT_ETIMEOUT
+    P.tdct_sync_status()  # the word was cleared
+    got, rec, _ = run_codec(img, 16)
+    want_sse, want_rec, _ = oc.codec_plane(host, M.T1, 16)
+    assert got == want_sse and np.array_equal(rec, want_rec)
+    P.tdct_sync_status()
