@@ -131,6 +131,31 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
                              int path, tdct_stream_t stream);
 
 /*
+ * tdct_codec_error_batched_noalloc -- tdct_codec_error_batched for callers
+ * that must not allocate device memory.  The paper has no counterpart: this
+ * is a deployment variant.  Some callers cannot call cudaMalloc (or let a
+ * library do it): a process whose own allocator has reserved the device
+ * memory up front, a real-time pipeline that forbids allocation after start
+ * (an allocation can synchronise the device and has unbounded latency), or
+ * code running where a stream-ordered pool is not available.  Here the
+ * block-offset table lives in a fixed array inside the library's device
+ * image, sized for TDCT_NOALLOC_MAX_PLANES planes (about 176 KB, held by
+ * every GPU that loads the library until the process exits).
+ *   Arguments, outputs and results are those of tdct_codec_error_batched
+ *   (the same kernels run), except that nplanes above TDCT_NOALLOC_MAX_PLANES
+ *   returns TDCT_EINVAL.  No device memory is allocated or freed.
+ *   The first call on a device looks up the array's device address (once
+ *   per device, with that device current); make that first call before any
+ *   stream capture.  Every call rewrites the shared array: calls whose work
+ *   overlaps on the GPU (for example on two streams) race on it and must be
+ *   serialised by the caller.
+ */
+#define TDCT_NOALLOC_MAX_PLANES 2048
+int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                                     const int32_t n[8], uint64_t* d_sse, double* d_psnr,
+                                     tdct_stream_t stream);
+
+/*
  * Batch plans: the same work as tdct_codec_error_batched, prepared once
  * (validation, block-offset table in device memory, launch configuration)
  * and replayed as one CUDA graph per launch.  The plan owns its device

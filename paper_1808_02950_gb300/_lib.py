@@ -33,6 +33,7 @@ N1 = (8, 18, 20, 18, 8, 18, 20, 18)
 
 EXPORTS = (
     "tdct_forward", "tdct_zonal_inverse", "tdct_codec_error", "tdct_codec_error_batched",
+    "tdct_codec_error_batched_noalloc",
     "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_destroy",
     "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
     "tdct_last_error", "tdct_version",
@@ -75,6 +76,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_zonal_inverse.argtypes = [vp, i32, i32, i32, vp, vp, i32, vp, i64, vp]
     L.tdct_codec_error.argtypes = [vp, i64, i32, i32, i32, vp, vp, i32, vp, i64, vp, vp, vp]
     L.tdct_codec_error_batched.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
+    L.tdct_codec_error_batched_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
     L.tdct_plan_create.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_void_p)]
     L.tdct_plan_launch.argtypes = [vp, vp, vp, vp]
     L.tdct_plan_kernel_count.argtypes = [vp]
@@ -191,6 +193,16 @@ def tdct_codec_error_batched(planes, sse, psnr=None, path=TDCT_PATH_AUTO, T=None
     tb, nb = _T_n(T, n)
     _check(load().tdct_codec_error_batched(ctypes.addressof(planes), len(planes), tb, nb,
                                            _ptr(sse), _ptr(psnr), int(path), _stream(stream)))
+
+
+NOALLOC_MAX_PLANES = 2048
+
+
+def tdct_codec_error_batched_noalloc(planes, sse, psnr=None, T=None, n=None, stream=None) -> None:
+    """tdct_codec_error_batched without any device allocation (fixed table)."""
+    tb, nb = _T_n(T, n)
+    _check(load().tdct_codec_error_batched_noalloc(ctypes.addressof(planes), len(planes), tb, nb,
+                                                   _ptr(sse), _ptr(psnr), _stream(stream)))
 
 
 class TdctPlan:

@@ -541,6 +541,74 @@ void tdct_plan_destroy(tdct_plan* plan) {
   delete plan;
 }
 
+// ---- batch without device allocation -------------------------------------------
+// The block-offset table of tdct_codec_error_batched_noalloc: descriptors,
+// then the per-plane sample counts, in one fixed device array.
+}  // extern "C"
+
+namespace {
+constexpr size_t kNoAllocDescBytes = sizeof(tdct::PlaneDesc) * TDCT_NOALLOC_MAX_PLANES;
+constexpr size_t kNoAllocBytes = kNoAllocDescBytes + sizeof(int64_t) * TDCT_NOALLOC_MAX_PLANES;
+}  // namespace
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once
+// per device; the host-side symbol is not a device address).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(TDCT_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc table)");
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return TDCT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                                     const int32_t n[8], uint64_t* d_sse, double* d_psnr,
+                                     tdct_stream_t stream) {
+  int rc = check_transform(T, n);
+  if (rc) return rc;
+  if (nplanes > TDCT_NOALLOC_MAX_PLANES)
+    return fail(TDCT_EINVAL,
+                "tdct_codec_error_batched_noalloc: %d planes exceed its fixed table of %d planes "
+                "(use tdct_codec_error_batched or split the batch)",
+                nplanes, TDCT_NOALLOC_MAX_PLANES);
+  if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
+    return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
+  std::vector<PlaneDesc> descs;
+  std::vector<Group> groups;
+  std::vector<int64_t> npix;
+  if ((rc = build_batch(planes, nplanes, descs, groups, npix))) return rc;
+  void* scratch = nullptr;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
+  PlaneDesc* d_descs = static_cast<PlaneDesc*>(scratch);
+  int64_t* d_npix = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + kNoAllocDescBytes);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(d_descs, descs.data(), sizeof(PlaneDesc) * descs.size(),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_npix, npix.data(), sizeof(int64_t) * npix.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = enqueue_batch(groups, d_descs, d_npix, nplanes,
+                      reinterpret_cast<unsigned long long*>(d_sse), d_psnr, s);
+  return e == cudaSuccess ? TDCT_OK : cuda_fail(e, "tdct_codec_error_batched_noalloc");
+}
+
 int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype, int r,
                          int precision, float* d_coef, void* d_recon, int64_t recon_pitch,
                          uint64_t* d_sse, double* d_psnr, tdct_stream_t stream) {
