@@ -151,6 +151,31 @@ class ClockSampler:
         }
 
 
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("tdct_device.cuh", "tdct_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1808_02950_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(blocks: int):
+    """DRAM bytes per launch of the fused codec from the committed ncu summary,
+    scaled to `blocks`; None when the kernel sources changed since the capture."""
+    import glob
+    import re
+
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "codec_u8_tma_kernel_*_full.md"))):
+        text = open(path).read()
+        m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+        m_t = re.search(r"traffic_bytes_per_block:\s*([0-9.]+)", text)
+        if m_h and m_t and m_h.group(1) == kernel_source_hash():
+            return float(m_t.group(1)) * blocks, os.path.basename(path)
+    return None, None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -251,6 +276,7 @@ def time_ours(args, dist, out):
     kernel_ms = statistics.mean(per_step)
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (kernel_ms / 1e3) / 1e9
+    traffic, traffic_src = profiled_traffic(wl.blocks) if args.workload == "batch_1024x1024" else (None, None)
     out.update({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
@@ -260,7 +286,8 @@ def time_ours(args, dist, out):
                    "inputs smaller than L2"},
         "hbm_gbs": achieved,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                     "peak_kind": peak_kind,
                      "algo_bytes_per_launch": algo_bytes, "kernel_ms": kernel_ms},
         "clocks": clk,
         "gpu_launches": plan.kernel_count() * args.steps,
@@ -334,11 +361,12 @@ def cpu_oracle_rate(planes_host, budget_s: float):
                 done_blocks += nb
                 done_planes += 1
 
-    with ThreadPoolExecutor(cores) as ex:
-        for f in [ex.submit(worker) for _ in range(cores)]:
+    threads = max(1, min(cores, len(planes_host)))
+    with ThreadPoolExecutor(threads) as ex:
+        for f in [ex.submit(worker) for _ in range(threads)]:
             f.result()
     dt = time.perf_counter() - t0
-    return done_blocks / dt, done_blocks, cores, done_planes
+    return done_blocks / dt, done_blocks, threads, done_planes
 
 
 def host_sample(wl, max_planes: int):
