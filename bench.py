@@ -45,6 +45,8 @@ def parse():
                     choices=["batch_1024x1024", "ragged_2000", "video_600x1080p", "single_512"])
     ap.add_argument("--images", type=int, default=1024,
                     help="images of batch_1024x1024 (smaller only for profiling captures)")
+    ap.add_argument("--path", default="butterfly", choices=["butterfly", "tensor", "auto"],
+                    help="forward-transform engine of the fused codec")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -245,7 +247,9 @@ def time_ours(args, dist, out):
     n = len(wl.planes)
     sse = torch.zeros(n, dtype=torch.int64, device=dev)
     psnr = torch.zeros(n, dtype=torch.float64, device=dev)
-    plan = P.tdct_plan_create(planes)
+    path = {"butterfly": P.TDCT_PATH_BUTTERFLY, "tensor": P.TDCT_PATH_TENSOR,
+            "auto": P.TDCT_PATH_AUTO}[args.path]
+    plan = P.tdct_plan_create(planes, path=path)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
         plan.launch(sse, psnr, stream)
@@ -281,7 +285,7 @@ def time_ours(args, dist, out):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32 (u8 in/out)", "data": "synthetic",
-        "config": {**wl.desc, "parallelism": f"replicas{dist.world}", "path": "butterfly",
+        "config": {**wl.desc, "parallelism": f"replicas{dist.world}", "path": args.path,
                    "l2": "inputs larger than L2 (no flush)" if algo_bytes > 256e6 else
                    "inputs smaller than L2"},
         "hbm_gbs": achieved,
@@ -304,7 +308,7 @@ def time_ours(args, dist, out):
         def e2e_step():
             for hb, db in zip(host_bufs, wl.storage):
                 db.copy_(hb, non_blocking=True)
-            P.tdct_codec_error_batched(planes, sse, psnr, stream=stream)
+            P.tdct_codec_error_batched(planes, sse, psnr, path=path, stream=stream)
             sse_h.copy_(sse, non_blocking=True)
             psnr_h.copy_(psnr, non_blocking=True)
 

@@ -61,7 +61,19 @@ enum tdct_dtype { TDCT_U8 = 0, TDCT_I16 = 1 };
 
 enum tdct_precision { TDCT_FP32 = 0, TDCT_BF16 = 1 };
 
-enum tdct_path { TDCT_PATH_AUTO = 0, TDCT_PATH_BUTTERFLY = 1, TDCT_PATH_TC_I8 = 2 };
+/*
+ * Forward-transform engines of the fused codec.
+ *   TDCT_PATH_BUTTERFLY  the fast algorithm of §5.1 on the CUDA cores.
+ *   TDCT_PATH_TENSOR     Z = T1 X T1^T as a GEMM on the tensor cores
+ *                        (tcgen05.mma; sm_103a has no int8 MMA, so pixels
+ *                        enter as exact fp16 values and the FP32 accumulation
+ *                        is exact).  Bit-identical results to the butterfly.
+ *                        Used for u8 planes with 16-byte aligned rows,
+ *                        W % 16 == 0 and H % 8 == 0; other planes of the batch
+ *                        take the butterfly.
+ *   TDCT_PATH_AUTO       the library's choice.
+ */
+enum tdct_path { TDCT_PATH_AUTO = 0, TDCT_PATH_BUTTERFLY = 1, TDCT_PATH_TENSOR = 2 };
 
 /*
  * tdct_forward -- forward 2-D transform of every block (§6.1, B = C_hat A
@@ -123,7 +135,9 @@ typedef struct tdct_plane {
  *   planes    host array of nplanes descriptors (1 <= nplanes <= 2^20)
  *   d_sse     output, uint64 [nplanes]
  *   d_psnr    output or NULL, double [nplanes]
- *   path      TDCT_PATH_AUTO or TDCT_PATH_BUTTERFLY
+ *   path      a tdct_path.  The first TDCT_PATH_TENSOR call on a device
+ *             uploads the tensor-core weight tables synchronously: make it
+ *             outside any stream capture.
  * Errors: as tdct_codec_error for any plane, TDCT_ENOMEM.
  */
 int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t T[64],

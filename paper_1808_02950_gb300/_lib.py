@@ -16,7 +16,7 @@ TDCT_OK, TDCT_EINVAL, TDCT_ENOTORTHO, TDCT_ECUDA = 0, 1, 2, 3
 TDCT_ETIMEOUT, TDCT_EDEVICE, TDCT_ENOMEM, TDCT_EUNSUPPORTED = 4, 5, 6, 7
 TDCT_U8, TDCT_I16 = 0, 1
 TDCT_FP32, TDCT_BF16 = 0, 1
-TDCT_PATH_AUTO, TDCT_PATH_BUTTERFLY, TDCT_PATH_TC_I8 = 0, 1, 2
+TDCT_PATH_AUTO, TDCT_PATH_BUTTERFLY, TDCT_PATH_TENSOR = 0, 1, 2
 
 # T1 of §4.1 and n = diag(T1 T1^T), the arguments the paper states (S = diag(1/sqrt(n))).
 T1 = (

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -24,6 +25,7 @@
 #include "tdct_classes.h"
 #include "tdct_dct.h"
 #include "tdct_kernels.cuh"
+#include "tdct_tc.h"
 
 namespace tdct {
 
@@ -122,6 +124,7 @@ CodecParams make_params(int r) {
     for (int j = 0; j < 8; ++j) cp.cmul[8 * i + j] = kept(r, i, j) ? q_of(i) * q_of(j) : 0;
   cp.status = status_word();
   cp.wait_limit = 2000000000ll;  // about a second of SM clock
+  if (const char* env = std::getenv("TDCT_CTAS_PER_SM")) cp.ctas_per_sm = std::atoi(env);
   if (g_inject_timeout.exchange(0)) {
     cp.test_hook = 1;
     cp.wait_limit = 20000000ll;
@@ -157,6 +160,20 @@ PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int
 }
 
 int64_t units_of(const PlaneDesc& d) { return (int64_t)d.nby * d.chunks; }
+
+cudaError_t dispatch_codec_tc(int r, const PlaneTable& tab, unsigned long long* sse,
+                              cudaStream_t s) {
+  const CodecParams cp = make_params(r);
+  switch (r_class(r)) {
+#define TDCT_CASE(R) \
+  case R:            \
+    return launch_codec_tc<R>(tab, cp, r, sse, s);
+    TDCT_FOR_EACH_CLASS(TDCT_CASE)
+#undef TDCT_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t dispatch_codec(int r, int dtype, const PlaneTable& tab, unsigned long long* sse,
                            int max_ctas, cudaStream_t s) {
@@ -307,7 +324,7 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
 // Enqueue the kernels of a batch whose descriptors live at d_descs (device).
 cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_descs,
                           const int64_t* d_npix, int nplanes, unsigned long long* sse,
-                          double* psnr, cudaStream_t s) {
+                          double* psnr, cudaStream_t s, int path = TDCT_PATH_AUTO) {
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long) * nplanes, s);
   if (e != cudaSuccess) return e;
   for (const Group& g : groups) {
@@ -317,7 +334,11 @@ cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_d
     tab.n = g.count;
     tab.total_units = g.units;
     tab.any_bulk = g.any_bulk;
-    if ((e = dispatch_codec(g.r, g.dtype, tab, sse, 0, s)) != cudaSuccess) return e;
+    if (path == TDCT_PATH_TENSOR && g.any_bulk && g.dtype == TDCT_U8)
+      e = dispatch_codec_tc(g.r, tab, sse, s);
+    else
+      e = dispatch_codec(g.r, g.dtype, tab, sse, 0, s);
+    if (e != cudaSuccess) return e;
   }
   if (psnr) {
     psnr_kernel<<<(nplanes + 255) / 256, 256, 0, s>>>(sse, d_npix, 0, psnr, nplanes);
@@ -335,6 +356,7 @@ using namespace tdct;
 
 struct tdct_plan {
   std::vector<Group> groups;
+  int path = TDCT_PATH_AUTO;
   int nplanes = 0;
   PlaneDesc* d_descs = nullptr;
   int64_t* d_npix = nullptr;
@@ -426,8 +448,8 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
                              tdct_stream_t stream) {
   int rc = check_transform(T, n);
   if (rc) return rc;
-  if (path != TDCT_PATH_AUTO && path != TDCT_PATH_BUTTERFLY)
-    return fail(TDCT_EUNSUPPORTED, "path %d is not implemented for batches", path);
+  if (path != TDCT_PATH_AUTO && path != TDCT_PATH_BUTTERFLY && path != TDCT_PATH_TENSOR)
+    return fail(TDCT_EUNSUPPORTED, "path %d is not a tdct_path", path);
   if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
     return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
   std::vector<PlaneDesc> descs;
@@ -435,6 +457,11 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
   std::vector<int64_t> npix;
   if ((rc = build_batch(planes, nplanes, descs, groups, npix))) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (path == TDCT_PATH_TENSOR) {
+    const uint16_t* table = nullptr;
+    const cudaError_t et = tc_prepare(&table);
+    if (et != cudaSuccess) return cuda_fail(et, "tensor-core weight tables");
+  }
   // Stream-ordered scratch for the block-offset table, freed after the kernels.
   const size_t bytes_desc = sizeof(PlaneDesc) * descs.size();
   const size_t bytes_npix = sizeof(int64_t) * npix.size();
@@ -448,7 +475,7 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
       (e = cudaMemcpyAsync(d_npix, npix.data(), bytes_npix, cudaMemcpyHostToDevice, s)) ==
           cudaSuccess)
     e = enqueue_batch(groups, d_descs, d_npix, nplanes,
-                      reinterpret_cast<unsigned long long*>(d_sse), d_psnr, s);
+                      reinterpret_cast<unsigned long long*>(d_sse), d_psnr, s, path);
   const cudaError_t ef = cudaFreeAsync(scratch, s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error_batched");
   if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
@@ -461,8 +488,8 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
   *out_plan = nullptr;
   int rc = check_transform(T, n);
   if (rc) return rc;
-  if (path != TDCT_PATH_AUTO && path != TDCT_PATH_BUTTERFLY)
-    return fail(TDCT_EUNSUPPORTED, "path %d is not implemented for batches", path);
+  if (path != TDCT_PATH_AUTO && path != TDCT_PATH_BUTTERFLY && path != TDCT_PATH_TENSOR)
+    return fail(TDCT_EUNSUPPORTED, "path %d is not a tdct_path", path);
   std::vector<PlaneDesc> descs;
   std::vector<int64_t> npix;
   tdct_plan* plan = new (std::nothrow) tdct_plan;
@@ -472,6 +499,15 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
     return rc;
   }
   plan->nplanes = nplanes;
+  plan->path = path;
+  if (path == TDCT_PATH_TENSOR) {
+    const uint16_t* table = nullptr;
+    const cudaError_t et = tc_prepare(&table);
+    if (et != cudaSuccess) {
+      delete plan;
+      return cuda_fail(et, "tensor-core weight tables");
+    }
+  }
   cudaError_t e = cudaMalloc(&plan->d_descs, sizeof(PlaneDesc) * descs.size());
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_npix, sizeof(int64_t) * npix.size());
   if (e != cudaSuccess) {
@@ -512,7 +548,8 @@ int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stre
     e = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     const cudaError_t ee = enqueue_batch(plan->groups, plan->d_descs, plan->d_npix,
-                                         plan->nplanes, sse, d_psnr, plan->capture_stream);
+                                         plan->nplanes, sse, d_psnr, plan->capture_stream,
+                                         plan->path);
     e = cudaStreamEndCapture(plan->capture_stream, &graph);
     if (ee != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);

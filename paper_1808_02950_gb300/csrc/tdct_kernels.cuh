@@ -154,7 +154,7 @@ struct CodecParams {
   int* status;           // device status word (TDCT_ETIMEOUT on a bounded wait giving up)
   long long wait_limit;  // clock cycles a bulk-copy wait may take before giving up
   int32_t test_hook;     // 1: the first copy of warp 0 is never issued (timeout test)
-  int32_t pad_;
+  int32_t ctas_per_sm;   // > 0: cap on resident CTAs per SM (launch tuning)
 };
 
 // Forward, zonal mask, scale by q_i q_j, inverse, round and clamp one block.
@@ -778,6 +778,10 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
       e = cudaFuncSetAttribute(codec_u8_tma_kernel<R, kStages>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
       if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(codec_u8_tma_kernel<R, kStages>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &resident_bulk, codec_u8_tma_kernel<R, kStages>, kThreads, kSmem);
       if (e != cudaSuccess) return e;
@@ -785,7 +789,9 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
     }
   }
   const bool bulk = DT == 0 && tab.any_bulk;
-  int64_t grid = (int64_t)(bulk ? resident_bulk : resident) * sms;
+  int per_sm = bulk ? resident_bulk : resident;
+  if (cp.ctas_per_sm > 0 && cp.ctas_per_sm < per_sm) per_sm = cp.ctas_per_sm;
+  int64_t grid = (int64_t)per_sm * sms;
   const int64_t by_work = (tab.total_units + kThreads / 32 - 1) / (kThreads / 32);
   if (by_work < grid) grid = by_work;
   if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;

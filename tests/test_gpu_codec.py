@@ -272,3 +272,78 @@ def test_bounded_wait_timeout_is_reported_and_context_survives():
     want_sse, want_rec, _ = oc.codec_plane(host, M.T1, 16)
     assert got == want_sse and np.array_equal(rec, want_rec)
     P.tdct_sync_status()
+
+
+# ---- the tensor-core forward (tcgen05.mma, exact fp16 inputs, FP32 accumulate) ----
+
+
+def _run_batch_path(views, rs, path, with_recon=True):
+    recons = [torch.full_like(v, 5) for v in views] if with_recon else None
+    planes = P.make_planes(views, rs, recons)
+    sse = torch.zeros(len(views), dtype=torch.int64, device=DEV)
+    psnr = torch.zeros(len(views), dtype=torch.float64, device=DEV)
+    P.tdct_codec_error_batched(planes, sse, psnr, path=path)
+    torch.cuda.synchronize()
+    return sse.cpu().numpy(), psnr.cpu().numpy(), recons
+
+
+@pytest.mark.parametrize("H,W", [(8, 16), (16, 512), (64, 1040), (48, 2048), (8, 4096)])
+def test_tensor_path_matches_oracle(H, W):
+    rng = np.random.default_rng(H * 11 + W)
+    host = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    img = torch.from_numpy(host).to(DEV)
+    for r in (1, 3, 8, 9, 10, 16, 17, 32, 33, 64):
+        sse, psnr, recons = _run_batch_path([img], [r], P.TDCT_PATH_TENSOR)
+        want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+        assert sse[0] == want_sse, f"r={r}"
+        assert np.array_equal(recons[0].cpu().numpy(), want_rec), f"r={r}"
+        sse2, _, _ = _run_batch_path([img], [r], P.TDCT_PATH_TENSOR, with_recon=False)
+        assert sse2[0] == want_sse
+
+
+def test_tensor_path_adversarial_and_mixed_batch():
+    blocks = synth.adversarial_blocks(DEV)  # 8 x 1072: eligible for the tensor path
+    rng = np.random.default_rng(31)
+    odd = torch.from_numpy(rng.integers(0, 256, (13, 11)).astype(np.uint8)).to(DEV)
+    res = torch.from_numpy(rng.integers(-255, 256, (16, 32)).astype(np.int16)).to(DEV)
+    views = [blocks, odd, res, blocks]
+    rs = [16, 10, 8, 64]
+    sse, _, recons = _run_batch_path(views, rs, P.TDCT_PATH_TENSOR)
+    for i, v in enumerate(views):
+        want_sse, want_rec, _ = oc.codec_plane(v.cpu().numpy(), M.T1, rs[i])
+        assert sse[i] == want_sse
+        assert np.array_equal(recons[i].cpu().numpy(), want_rec)
+
+
+def test_tensor_path_equals_butterfly_on_many_images():
+    imgs, r = synth.batch_1024x1024(DEV, n=64)
+    views = [imgs[i] for i in range(64)]
+    a, pa, ra = _run_batch_path(views, [r] * 64, P.TDCT_PATH_TENSOR)
+    b, pb, rb = _run_batch_path(views, [r] * 64, P.TDCT_PATH_BUTTERFLY)
+    assert np.array_equal(a, b) and np.array_equal(pa, pb)
+    for i in (0, 31, 63):
+        assert torch.equal(ra[i], rb[i])
+    assert a[0] == oc.codec_plane(imgs[0].cpu().numpy(), M.T1, r, want_recon=False)[0]
+    planes = P.make_planes(views, [r] * 64)
+    plan = P.tdct_plan_create(planes, path=P.TDCT_PATH_TENSOR)
+    sse = torch.zeros(64, dtype=torch.int64, device=DEV)
+    for _ in range(2):
+        plan.launch(sse)
+        torch.cuda.synchronize()
+        assert np.array_equal(sse.cpu().numpy(), b)
+    plan.close()
+
+
+def test_tensor_path_bounded_wait_timeout():
+    img = torch.from_numpy(np.random.default_rng(3).integers(0, 256, (64, 1024)).astype(np.uint8)).to(DEV)
+    P.tdct_sync_status()
+    _run_batch_path([img], [16], P.TDCT_PATH_TENSOR)  # tables built, kernel loaded
+    P.tdct_debug_inject_wait_timeout(True)
+    _run_batch_path([img], [16], P.TDCT_PATH_TENSOR)
+    with pytest.raises(P.TdctError) as e:
+        P.tdct_sync_status()
+    assert e.value.code == 4
+    sse, _, recons = _run_batch_path([img], [16], P.TDCT_PATH_TENSOR)
+    want_sse, want_rec, _ = oc.codec_plane(img.cpu().numpy(), M.T1, 16)
+    assert sse[0] == want_sse and np.array_equal(recons[0].cpu().numpy(), want_rec)
+    P.tdct_sync_status()
