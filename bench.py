@@ -45,8 +45,8 @@ def parse():
                     choices=["batch_1024x1024", "ragged_2000", "video_600x1080p", "single_512"])
     ap.add_argument("--images", type=int, default=1024,
                     help="images of batch_1024x1024 (smaller only for profiling captures)")
-    ap.add_argument("--path", default="butterfly", choices=["butterfly", "tensor", "auto"],
-                    help="forward-transform engine of the fused codec")
+    ap.add_argument("--path", default="auto", choices=["butterfly", "tensor", "auto"],
+                    help="forward-transform engine of the fused codec (auto: the plan autotunes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -178,6 +178,14 @@ def profiled_traffic(blocks: int):
     return None, None
 
 
+def aggregate(dist, blocks_local: int, ms_local: float, steps: int):
+    """Whole-job throughput of replicas: the units all ranks processed over
+    the slowest rank's time.  Returns (blocks/s, max ms, total blocks)."""
+    total_ms = dist.max(ms_local)
+    blocks_all = dist.sum(blocks_local)
+    return blocks_all * steps / (total_ms / 1e3), total_ms, blocks_all
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -250,6 +258,7 @@ def time_ours(args, dist, out):
     path = {"butterfly": P.TDCT_PATH_BUTTERFLY, "tensor": P.TDCT_PATH_TENSOR,
             "auto": P.TDCT_PATH_AUTO}[args.path]
     plan = P.tdct_plan_create(planes, path=path)
+    plan_cfg = plan.config()
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
         plan.launch(sse, psnr, stream)
@@ -268,10 +277,8 @@ def time_ours(args, dist, out):
     dist.barrier()
     clk = clocks.stop()
     per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[args.steps])
-    total_ms = dist.max(total_ms)
-    blocks_all = dist.sum(wl.blocks)
-    value = blocks_all * args.steps / (total_ms / 1e3)
+    value, total_ms, blocks_all = aggregate(dist, wl.blocks, ev[0].elapsed_time(ev[args.steps]),
+                                            args.steps)
     step_ms = total_ms / args.steps
 
     # Roofline of the dominant kernel (the fused codec): algorithmic bytes =
@@ -285,7 +292,8 @@ def time_ours(args, dist, out):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32 (u8 in/out)", "data": "synthetic",
-        "config": {**wl.desc, "parallelism": f"replicas{dist.world}", "path": args.path,
+        "config": {**wl.desc, "parallelism": f"replicas{dist.world}", "path": plan_cfg["path"],
+                   "ctas_per_sm": plan_cfg["ctas_per_sm"], "autotuned": args.path == "auto",
                    "l2": "inputs larger than L2 (no flush)" if algo_bytes > 256e6 else
                    "inputs smaller than L2"},
         "hbm_gbs": achieved,
@@ -308,7 +316,9 @@ def time_ours(args, dist, out):
         def e2e_step():
             for hb, db in zip(host_bufs, wl.storage):
                 db.copy_(hb, non_blocking=True)
-            P.tdct_codec_error_batched(planes, sse, psnr, path=path, stream=stream)
+            P.tdct_codec_error_batched(planes, sse, psnr, stream=stream,
+                                       path={"butterfly": P.TDCT_PATH_BUTTERFLY,
+                                             "tensor": P.TDCT_PATH_TENSOR}[plan_cfg["path"]])
             sse_h.copy_(sse, non_blocking=True)
             psnr_h.copy_(psnr, non_blocking=True)
 

@@ -177,8 +177,18 @@ int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, cons
  */
 typedef struct tdct_plan tdct_plan;
 
+/*
+ * path: a tdct_path.  TDCT_PATH_AUTO autotunes: every candidate engine and
+ * launch shape (CTAs per SM) runs on the plan's own planes (their inputs
+ * must hold valid data; reconstructions are written) and the fastest is
+ * kept.  Creation synchronises the device work it enqueues; call it outside
+ * stream capture.
+ */
 int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
                      const int32_t n[8], int path, tdct_plan** out_plan);
+/* The configuration a plan uses: engine (tdct_path), CTAs per SM (0 = the
+ * library default) and, for autotuned plans, the tuned step time in ms. */
+int tdct_plan_config(const tdct_plan* plan, int* path, int* ctas_per_sm, float* tuned_ms);
 /* Enqueue one run of the plan on `stream`: SSE (and PSNR) for every plane. */
 int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stream_t stream);
 /* Kernel launches one tdct_plan_launch performs (for launch accounting). */

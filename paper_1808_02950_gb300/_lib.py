@@ -34,7 +34,8 @@ N1 = (8, 18, 20, 18, 8, 18, 20, 18)
 EXPORTS = (
     "tdct_forward", "tdct_zonal_inverse", "tdct_codec_error", "tdct_codec_error_batched",
     "tdct_codec_error_batched_noalloc",
-    "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_destroy",
+    "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_config",
+    "tdct_plan_destroy",
     "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
     "tdct_last_error", "tdct_version",
 )
@@ -80,6 +81,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_plan_create.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_void_p)]
     L.tdct_plan_launch.argtypes = [vp, vp, vp, vp]
     L.tdct_plan_kernel_count.argtypes = [vp]
+    L.tdct_plan_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_float)]
     L.tdct_plan_destroy.argtypes = [vp]
     L.tdct_plan_destroy.restype = None
     L.tdct_dct_codec_error.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp, vp, i64, vp, vp, vp]
@@ -222,6 +225,14 @@ class TdctPlan:
 
     def kernel_count(self) -> int:
         return load().tdct_plan_kernel_count(self._h)
+
+    def config(self) -> dict:
+        """The engine, CTAs per SM and tuned time the plan uses."""
+        path, cps, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _check(load().tdct_plan_config(self._h, ctypes.byref(path), ctypes.byref(cps), ctypes.byref(ms)))
+        names = {TDCT_PATH_BUTTERFLY: "butterfly", TDCT_PATH_TENSOR: "tensor"}
+        return {"path": names.get(path.value, path.value), "ctas_per_sm": cps.value,
+                "tuned_ms": ms.value}
 
     def close(self) -> None:
         if self._h:

@@ -117,13 +117,14 @@ int* status_word() {
   return static_cast<int*>(addr[dev]);
 }
 
-CodecParams make_params(int r) {
+CodecParams make_params(int r, int ctas_per_sm = 0) {
   CodecParams cp;
   std::memset(&cp, 0, sizeof cp);
   for (int i = 0; i < 8; ++i)
     for (int j = 0; j < 8; ++j) cp.cmul[8 * i + j] = kept(r, i, j) ? q_of(i) * q_of(j) : 0;
   cp.status = status_word();
   cp.wait_limit = 2000000000ll;  // about a second of SM clock
+  cp.ctas_per_sm = ctas_per_sm;
   if (const char* env = std::getenv("TDCT_CTAS_PER_SM")) cp.ctas_per_sm = std::atoi(env);
   if (g_inject_timeout.exchange(0)) {
     cp.test_hook = 1;
@@ -162,8 +163,8 @@ PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int
 int64_t units_of(const PlaneDesc& d) { return (int64_t)d.nby * d.chunks; }
 
 cudaError_t dispatch_codec_tc(int r, const PlaneTable& tab, unsigned long long* sse,
-                              cudaStream_t s) {
-  const CodecParams cp = make_params(r);
+                              cudaStream_t s, int ctas_per_sm = 0) {
+  const CodecParams cp = make_params(r, ctas_per_sm);
   switch (r_class(r)) {
 #define TDCT_CASE(R) \
   case R:            \
@@ -176,8 +177,8 @@ cudaError_t dispatch_codec_tc(int r, const PlaneTable& tab, unsigned long long* 
 }
 
 cudaError_t dispatch_codec(int r, int dtype, const PlaneTable& tab, unsigned long long* sse,
-                           int max_ctas, cudaStream_t s) {
-  const CodecParams cp = make_params(r);
+                           int max_ctas, cudaStream_t s, int ctas_per_sm = 0) {
+  const CodecParams cp = make_params(r, ctas_per_sm);
   switch (r_class(r)) {
 #define TDCT_CASE(R)                                                     \
   case R:                                                                \
@@ -324,7 +325,8 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
 // Enqueue the kernels of a batch whose descriptors live at d_descs (device).
 cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_descs,
                           const int64_t* d_npix, int nplanes, unsigned long long* sse,
-                          double* psnr, cudaStream_t s, int path = TDCT_PATH_AUTO) {
+                          double* psnr, cudaStream_t s, int path = TDCT_PATH_AUTO,
+                          int ctas_per_sm = 0) {
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long) * nplanes, s);
   if (e != cudaSuccess) return e;
   for (const Group& g : groups) {
@@ -335,9 +337,9 @@ cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_d
     tab.total_units = g.units;
     tab.any_bulk = g.any_bulk;
     if (path == TDCT_PATH_TENSOR && g.any_bulk && g.dtype == TDCT_U8)
-      e = dispatch_codec_tc(g.r, tab, sse, s);
+      e = dispatch_codec_tc(g.r, tab, sse, s, ctas_per_sm);
     else
-      e = dispatch_codec(g.r, g.dtype, tab, sse, 0, s);
+      e = dispatch_codec(g.r, g.dtype, tab, sse, 0, s, ctas_per_sm);
     if (e != cudaSuccess) return e;
   }
   if (psnr) {
@@ -356,7 +358,9 @@ using namespace tdct;
 
 struct tdct_plan {
   std::vector<Group> groups;
-  int path = TDCT_PATH_AUTO;
+  int path = TDCT_PATH_AUTO;   // engine used by launches (never AUTO after creation)
+  int ctas_per_sm = 0;         // launch shape (0 = the library default)
+  float tuned_ms = 0.f;        // time of the chosen configuration (autotuned plans)
   int nplanes = 0;
   PlaneDesc* d_descs = nullptr;
   int64_t* d_npix = nullptr;
@@ -366,6 +370,66 @@ struct tdct_plan {
   double* exec_psnr = nullptr;
   std::mutex mu;
 };
+
+namespace {
+
+// Autotuner of TDCT_PATH_AUTO plans: runs every candidate (engine x CTAs per
+// SM) on the plan's own planes (reconstructions are written, SSE goes to a
+// scratch buffer) and keeps the fastest.  Two untimed runs, then the median
+// of three timed runs per candidate, on the plan's private stream.
+int autotune_plan(tdct_plan* plan) {
+  bool any_u8_bulk = false;
+  for (const Group& g : plan->groups) any_u8_bulk |= (g.any_bulk && g.dtype == TDCT_U8);
+  struct Cand { int path, cps; };
+  std::vector<Cand> cands = {{TDCT_PATH_BUTTERFLY, 0}, {TDCT_PATH_BUTTERFLY, 1}};
+  if (any_u8_bulk) {
+    const uint16_t* table = nullptr;
+    if (tc_prepare(&table) == cudaSuccess) {
+      cands.push_back({TDCT_PATH_TENSOR, 0});
+      cands.push_back({TDCT_PATH_TENSOR, 3});
+    }
+  }
+  cudaStream_t s = plan->capture_stream;
+  unsigned long long* sse = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&sse),
+                                  sizeof(unsigned long long) * plan->nplanes, s);
+  if (e != cudaSuccess) return fail(TDCT_ENOMEM, "autotune scratch: %s", cudaGetErrorString(e));
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  float best = 3.4e38f;
+  Cand pick = cands[0];
+  for (const Cand& c : cands) {
+    float t[3] = {0, 0, 0};
+    for (int it = 0; it < 5 && e == cudaSuccess; ++it) {
+      if (it >= 2) e = cudaEventRecord(ev0, s);
+      if (e == cudaSuccess)
+        e = enqueue_batch(plan->groups, plan->d_descs, plan->d_npix, plan->nplanes, sse, nullptr,
+                          s, c.path, c.cps);
+      if (e == cudaSuccess && it >= 2) e = cudaEventRecord(ev1, s);
+      if (e == cudaSuccess && it >= 2) e = cudaEventSynchronize(ev1);
+      if (e == cudaSuccess && it >= 2) e = cudaEventElapsedTime(&t[it - 2], ev0, ev1);
+    }
+    if (e != cudaSuccess) break;
+    std::sort(t, t + 3);
+    if (t[1] < best) {
+      best = t[1];
+      pick = c;
+    }
+  }
+  cudaFreeAsync(sse, s);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  if (es != cudaSuccess) return cuda_fail(es, "autotune");
+  plan->path = pick.path;
+  plan->ctas_per_sm = pick.cps;
+  plan->tuned_ms = best;
+  return TDCT_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -524,7 +588,22 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
     tdct_plan_destroy(plan);
     return cuda_fail(e, "tdct_plan_create");
   }
+  if (path == TDCT_PATH_AUTO) {
+    plan->path = TDCT_PATH_BUTTERFLY;
+    if ((rc = autotune_plan(plan))) {
+      tdct_plan_destroy(plan);
+      return rc;
+    }
+  }
   *out_plan = plan;
+  return TDCT_OK;
+}
+
+int tdct_plan_config(const tdct_plan* plan, int* path, int* ctas_per_sm, float* tuned_ms) {
+  if (!plan) return fail(TDCT_EINVAL, "plan is NULL");
+  if (path) *path = plan->path;
+  if (ctas_per_sm) *ctas_per_sm = plan->ctas_per_sm;
+  if (tuned_ms) *tuned_ms = plan->tuned_ms;
   return TDCT_OK;
 }
 
@@ -549,7 +628,7 @@ int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stre
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     const cudaError_t ee = enqueue_batch(plan->groups, plan->d_descs, plan->d_npix,
                                          plan->nplanes, sse, d_psnr, plan->capture_stream,
-                                         plan->path);
+                                         plan->path, plan->ctas_per_sm);
     e = cudaStreamEndCapture(plan->capture_stream, &graph);
     if (ee != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);

@@ -347,3 +347,25 @@ def test_tensor_path_bounded_wait_timeout():
     want_sse, want_rec, _ = oc.codec_plane(img.cpu().numpy(), M.T1, 16)
     assert sse[0] == want_sse and np.array_equal(recons[0].cpu().numpy(), want_rec)
     P.tdct_sync_status()
+
+
+def test_autotuned_plan_is_correct_and_reports_its_choice():
+    rng = np.random.default_rng(41)
+    hosts = [rng.integers(0, 256, (64, 1024)).astype(np.uint8) for _ in range(6)]
+    views = [torch.from_numpy(h).to(DEV) for h in hosts]
+    odd = rng.integers(-255, 256, (13, 24)).astype(np.int16)
+    hosts.append(odd)
+    views.append(torch.from_numpy(odd).to(DEV))
+    rs = [16, 16, 4, 32, 10, 64, 8]
+    recons = [torch.zeros_like(v) for v in views]
+    plan = P.tdct_plan_create(P.make_planes(views, rs, recons), path=P.TDCT_PATH_AUTO)
+    cfg = plan.config()
+    assert cfg["path"] in ("butterfly", "tensor") and cfg["tuned_ms"] > 0
+    sse = torch.zeros(len(views), dtype=torch.int64, device=DEV)
+    plan.launch(sse)
+    torch.cuda.synchronize()
+    for i, h in enumerate(hosts):
+        want_sse, want_rec, _ = oc.codec_plane(h, M.T1, rs[i])
+        assert int(sse[i]) == want_sse
+        assert np.array_equal(recons[i].cpu().numpy(), want_rec)
+    plan.close()
