@@ -45,7 +45,8 @@ def parse():
                     choices=["batch_1024x1024", "ragged_2000", "video_600x1080p", "single_512"])
     ap.add_argument("--images", type=int, default=1024,
                     help="images of batch_1024x1024 (smaller only for profiling captures)")
-    ap.add_argument("--path", default="auto", choices=["butterfly", "tensor", "auto"],
+    ap.add_argument("--path", default="auto",
+                    choices=["butterfly", "tensor", "tensor_pipelined", "auto"],
                     help="forward-transform engine of the fused codec (auto: the plan autotunes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -256,7 +257,7 @@ def time_ours(args, dist, out):
     sse = torch.zeros(n, dtype=torch.int64, device=dev)
     psnr = torch.zeros(n, dtype=torch.float64, device=dev)
     path = {"butterfly": P.TDCT_PATH_BUTTERFLY, "tensor": P.TDCT_PATH_TENSOR,
-            "auto": P.TDCT_PATH_AUTO}[args.path]
+            "tensor_pipelined": P.TDCT_PATH_TENSOR_PIPELINED, "auto": P.TDCT_PATH_AUTO}[args.path]
     plan = P.tdct_plan_create(planes, path=path)
     plan_cfg = plan.config()
     stream = torch.cuda.current_stream()
@@ -318,7 +319,9 @@ def time_ours(args, dist, out):
                 db.copy_(hb, non_blocking=True)
             P.tdct_codec_error_batched(planes, sse, psnr, stream=stream,
                                        path={"butterfly": P.TDCT_PATH_BUTTERFLY,
-                                             "tensor": P.TDCT_PATH_TENSOR}[plan_cfg["path"]])
+                                             "tensor": P.TDCT_PATH_TENSOR,
+                                             "tensor_pipelined": P.TDCT_PATH_TENSOR_PIPELINED}[
+                                                 plan_cfg["path"]])
             sse_h.copy_(sse, non_blocking=True)
             psnr_h.copy_(psnr, non_blocking=True)
 

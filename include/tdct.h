@@ -71,9 +71,18 @@ enum tdct_precision { TDCT_FP32 = 0, TDCT_BF16 = 1 };
  *                        Used for u8 planes with 16-byte aligned rows,
  *                        W % 16 == 0 and H % 8 == 0; other planes of the batch
  *                        take the butterfly.
- *   TDCT_PATH_AUTO       the library's choice.
+ *   TDCT_PATH_TENSOR_PIPELINED
+ *                        the tensor engine with the GEMM of the next tile
+ *                        running while the current tile is computed
+ *                        (faster at large r, slower at small r).
+ *   TDCT_PATH_AUTO       the library's choice (plans: autotuned).
  */
-enum tdct_path { TDCT_PATH_AUTO = 0, TDCT_PATH_BUTTERFLY = 1, TDCT_PATH_TENSOR = 2 };
+enum tdct_path {
+  TDCT_PATH_AUTO = 0,
+  TDCT_PATH_BUTTERFLY = 1,
+  TDCT_PATH_TENSOR = 2,
+  TDCT_PATH_TENSOR_PIPELINED = 3
+};
 
 /*
  * tdct_forward -- forward 2-D transform of every block (§6.1, B = C_hat A

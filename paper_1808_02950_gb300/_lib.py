@@ -16,7 +16,7 @@ TDCT_OK, TDCT_EINVAL, TDCT_ENOTORTHO, TDCT_ECUDA = 0, 1, 2, 3
 TDCT_ETIMEOUT, TDCT_EDEVICE, TDCT_ENOMEM, TDCT_EUNSUPPORTED = 4, 5, 6, 7
 TDCT_U8, TDCT_I16 = 0, 1
 TDCT_FP32, TDCT_BF16 = 0, 1
-TDCT_PATH_AUTO, TDCT_PATH_BUTTERFLY, TDCT_PATH_TENSOR = 0, 1, 2
+TDCT_PATH_AUTO, TDCT_PATH_BUTTERFLY, TDCT_PATH_TENSOR, TDCT_PATH_TENSOR_PIPELINED = 0, 1, 2, 3
 
 # T1 of §4.1 and n = diag(T1 T1^T), the arguments the paper states (S = diag(1/sqrt(n))).
 T1 = (
@@ -230,7 +230,8 @@ class TdctPlan:
         """The engine, CTAs per SM and tuned time the plan uses."""
         path, cps, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
         _check(load().tdct_plan_config(self._h, ctypes.byref(path), ctypes.byref(cps), ctypes.byref(ms)))
-        names = {TDCT_PATH_BUTTERFLY: "butterfly", TDCT_PATH_TENSOR: "tensor"}
+        names = {TDCT_PATH_BUTTERFLY: "butterfly", TDCT_PATH_TENSOR: "tensor",
+                 TDCT_PATH_TENSOR_PIPELINED: "tensor_pipelined"}
         return {"path": names.get(path.value, path.value), "ctas_per_sm": cps.value,
                 "tuned_ms": ms.value}
 

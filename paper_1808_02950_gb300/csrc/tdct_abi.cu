@@ -117,7 +117,7 @@ int* status_word() {
   return static_cast<int*>(addr[dev]);
 }
 
-CodecParams make_params(int r, int ctas_per_sm = 0) {
+CodecParams make_params(int r, int ctas_per_sm = 0, int tc_variant = 0) {
   CodecParams cp;
   std::memset(&cp, 0, sizeof cp);
   for (int i = 0; i < 8; ++i)
@@ -125,6 +125,7 @@ CodecParams make_params(int r, int ctas_per_sm = 0) {
   cp.status = status_word();
   cp.wait_limit = 2000000000ll;  // about a second of SM clock
   cp.ctas_per_sm = ctas_per_sm;
+  cp.tc_variant = tc_variant;
   if (const char* env = std::getenv("TDCT_CTAS_PER_SM")) cp.ctas_per_sm = std::atoi(env);
   if (g_inject_timeout.exchange(0)) {
     cp.test_hook = 1;
@@ -163,8 +164,8 @@ PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int
 int64_t units_of(const PlaneDesc& d) { return (int64_t)d.nby * d.chunks; }
 
 cudaError_t dispatch_codec_tc(int r, const PlaneTable& tab, unsigned long long* sse,
-                              cudaStream_t s, int ctas_per_sm = 0) {
-  const CodecParams cp = make_params(r, ctas_per_sm);
+                              cudaStream_t s, int ctas_per_sm = 0, int tc_variant = 0) {
+  const CodecParams cp = make_params(r, ctas_per_sm, tc_variant);
   switch (r_class(r)) {
 #define TDCT_CASE(R) \
   case R:            \
@@ -326,7 +327,7 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
 cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_descs,
                           const int64_t* d_npix, int nplanes, unsigned long long* sse,
                           double* psnr, cudaStream_t s, int path = TDCT_PATH_AUTO,
-                          int ctas_per_sm = 0) {
+                          int ctas_per_sm = 0, int tc_variant = 0) {
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long) * nplanes, s);
   if (e != cudaSuccess) return e;
   for (const Group& g : groups) {
@@ -336,8 +337,10 @@ cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_d
     tab.n = g.count;
     tab.total_units = g.units;
     tab.any_bulk = g.any_bulk;
-    if (path == TDCT_PATH_TENSOR && g.any_bulk && g.dtype == TDCT_U8)
-      e = dispatch_codec_tc(g.r, tab, sse, s, ctas_per_sm);
+    const bool tensor = path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED;
+    if (tensor && g.any_bulk && g.dtype == TDCT_U8)
+      e = dispatch_codec_tc(g.r, tab, sse, s, ctas_per_sm,
+                            path == TDCT_PATH_TENSOR_PIPELINED ? 1 : tc_variant);
     else
       e = dispatch_codec(g.r, g.dtype, tab, sse, 0, s, ctas_per_sm);
     if (e != cudaSuccess) return e;
@@ -360,6 +363,7 @@ struct tdct_plan {
   std::vector<Group> groups;
   int path = TDCT_PATH_AUTO;   // engine used by launches (never AUTO after creation)
   int ctas_per_sm = 0;         // launch shape (0 = the library default)
+  int tc_variant = 0;          // tensor engine: 0 one tile at a time, 1 pipelined
   float tuned_ms = 0.f;        // time of the chosen configuration (autotuned plans)
   int nplanes = 0;
   PlaneDesc* d_descs = nullptr;
@@ -380,13 +384,14 @@ namespace {
 int autotune_plan(tdct_plan* plan) {
   bool any_u8_bulk = false;
   for (const Group& g : plan->groups) any_u8_bulk |= (g.any_bulk && g.dtype == TDCT_U8);
-  struct Cand { int path, cps; };
-  std::vector<Cand> cands = {{TDCT_PATH_BUTTERFLY, 0}, {TDCT_PATH_BUTTERFLY, 1}};
+  struct Cand { int path, cps, variant; };
+  std::vector<Cand> cands = {{TDCT_PATH_BUTTERFLY, 0, 0}, {TDCT_PATH_BUTTERFLY, 1, 0}};
   if (any_u8_bulk) {
     const uint16_t* table = nullptr;
     if (tc_prepare(&table) == cudaSuccess) {
-      cands.push_back({TDCT_PATH_TENSOR, 0});
-      cands.push_back({TDCT_PATH_TENSOR, 3});
+      cands.push_back({TDCT_PATH_TENSOR, 0, 0});
+      cands.push_back({TDCT_PATH_TENSOR, 3, 0});
+      cands.push_back({TDCT_PATH_TENSOR, 0, 1});
     }
   }
   cudaStream_t s = plan->capture_stream;
@@ -405,7 +410,7 @@ int autotune_plan(tdct_plan* plan) {
       if (it >= 2) e = cudaEventRecord(ev0, s);
       if (e == cudaSuccess)
         e = enqueue_batch(plan->groups, plan->d_descs, plan->d_npix, plan->nplanes, sse, nullptr,
-                          s, c.path, c.cps);
+                          s, c.path, c.cps, c.variant);
       if (e == cudaSuccess && it >= 2) e = cudaEventRecord(ev1, s);
       if (e == cudaSuccess && it >= 2) e = cudaEventSynchronize(ev1);
       if (e == cudaSuccess && it >= 2) e = cudaEventElapsedTime(&t[it - 2], ev0, ev1);
@@ -423,8 +428,10 @@ int autotune_plan(tdct_plan* plan) {
   cudaEventDestroy(ev1);
   if (e != cudaSuccess) return cuda_fail(e, "autotune");
   if (es != cudaSuccess) return cuda_fail(es, "autotune");
-  plan->path = pick.path;
+  plan->path = pick.path == TDCT_PATH_TENSOR && pick.variant == 1 ? TDCT_PATH_TENSOR_PIPELINED
+                                                                   : pick.path;
   plan->ctas_per_sm = pick.cps;
+  plan->tc_variant = pick.variant;
   plan->tuned_ms = best;
   return TDCT_OK;
 }
@@ -512,7 +519,7 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
                              tdct_stream_t stream) {
   int rc = check_transform(T, n);
   if (rc) return rc;
-  if (path != TDCT_PATH_AUTO && path != TDCT_PATH_BUTTERFLY && path != TDCT_PATH_TENSOR)
+  if (path < TDCT_PATH_AUTO || path > TDCT_PATH_TENSOR_PIPELINED)
     return fail(TDCT_EUNSUPPORTED, "path %d is not a tdct_path", path);
   if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
     return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
@@ -521,7 +528,7 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
   std::vector<int64_t> npix;
   if ((rc = build_batch(planes, nplanes, descs, groups, npix))) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (path == TDCT_PATH_TENSOR) {
+  if (path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED) {
     const uint16_t* table = nullptr;
     const cudaError_t et = tc_prepare(&table);
     if (et != cudaSuccess) return cuda_fail(et, "tensor-core weight tables");
@@ -552,7 +559,7 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
   *out_plan = nullptr;
   int rc = check_transform(T, n);
   if (rc) return rc;
-  if (path != TDCT_PATH_AUTO && path != TDCT_PATH_BUTTERFLY && path != TDCT_PATH_TENSOR)
+  if (path < TDCT_PATH_AUTO || path > TDCT_PATH_TENSOR_PIPELINED)
     return fail(TDCT_EUNSUPPORTED, "path %d is not a tdct_path", path);
   std::vector<PlaneDesc> descs;
   std::vector<int64_t> npix;
@@ -564,7 +571,7 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
   }
   plan->nplanes = nplanes;
   plan->path = path;
-  if (path == TDCT_PATH_TENSOR) {
+  if (path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED) {
     const uint16_t* table = nullptr;
     const cudaError_t et = tc_prepare(&table);
     if (et != cudaSuccess) {
@@ -628,7 +635,7 @@ int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stre
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     const cudaError_t ee = enqueue_batch(plan->groups, plan->d_descs, plan->d_npix,
                                          plan->nplanes, sse, d_psnr, plan->capture_stream,
-                                         plan->path, plan->ctas_per_sm);
+                                         plan->path, plan->ctas_per_sm, plan->tc_variant);
     e = cudaStreamEndCapture(plan->capture_stream, &graph);
     if (ee != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);

@@ -155,6 +155,8 @@ struct CodecParams {
   long long wait_limit;  // clock cycles a bulk-copy wait may take before giving up
   int32_t test_hook;     // 1: the first copy of warp 0 is never issued (timeout test)
   int32_t ctas_per_sm;   // > 0: cap on resident CTAs per SM (launch tuning)
+  int32_t tc_variant;    // tensor engine: 0 one tile at a time, 1 software-pipelined
+  int32_t pad_;
 };
 
 // Forward, zonal mask, scale by q_i q_j, inverse, round and clamp one block.
@@ -380,6 +382,12 @@ __device__ __forceinline__ uint2 round_pack_row_u8(const uint32_t n2[8]) {
   return make_uint2(__byte_perm(c01, c23, 0x6420u), __byte_perm(c45, c67, 0x6420u));
 }
 
+// 1: accumulate each row's SSE terms into one running sum (a dependency
+// chain across rows); 0: form each row's terms independently.
+#ifndef TDCT_SSE_CHAIN
+#define TDCT_SSE_CHAIN 1
+#endif
+
 // Inverse of one block from its kept, scaled coefficients w (doubled and
 // biased), streamed by rows into rounding, SSE terms and the store.
 // `valid_cols` = samples of each row inside the plane (8 when full),
@@ -414,9 +422,16 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8(const uint32_t w[64], co
       y.x &= (uint32_t)m;
       y.y &= (uint32_t)(m >> 32);
     }
+#if TDCT_SSE_CHAIN
     acc = __dp4a(y.x, y.x, acc);
     acc = __dp4a(y.y, y.y, acc);
     acc -= 2u * __dp4a(x[k].x, y.x, __dp4a(x[k].y, y.y, 0u));
+#else
+    // per-row partials are independent; only the final add joins them
+    const uint32_t yy = __dp4a(y.x, y.x, __dp4a(y.y, y.y, 0u));
+    const uint32_t xy = __dp4a(x[k].x, y.x, __dp4a(x[k].y, y.y, 0u));
+    acc += yy - 2u * xy;
+#endif
     if (store && full) out_row0[(int64_t)k * (out_pitch >> 3)] = y;
     if (store && !full && k < valid_rows) {
       uint8_t* row = reinterpret_cast<uint8_t*>(out_row0) + (int64_t)k * out_pitch;
@@ -628,8 +643,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   return true;
 }
 
+// Threads per CTA of the bulk-copy ring kernel and the resident CTAs per SM
+// it is compiled for (registers <= 65536 / (threads * CTAs)).
+#ifndef TDCT_RING_THREADS
+#define TDCT_RING_THREADS 256
+#endif
+#ifndef TDCT_RING_MINB
+#define TDCT_RING_MINB (512 / TDCT_RING_THREADS)
+#endif
+
 template <int R, int STAGES>
-__global__ void __launch_bounds__(256, TDCT_U8_MINB)
+__global__ void __launch_bounds__(TDCT_RING_THREADS, TDCT_RING_MINB)
     codec_u8_tma_kernel(const PlaneTable tab, const CodecParams cp,
                         unsigned long long* __restrict__ sse_out) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -764,8 +788,9 @@ template <int R, int DT>
 cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned long long* sse,
                          int max_ctas, cudaStream_t s) {
   constexpr int kThreads = 256;
+  constexpr int kRingThreads = TDCT_RING_THREADS;
   constexpr int kStages = TDCT_U8_STAGES;
-  constexpr size_t kSmem = (size_t)(kThreads / 32) * kStages * (kUnitBytes + 8);
+  constexpr size_t kSmem = (size_t)(kRingThreads / 32) * kStages * (kUnitBytes + 8);
   static int resident = 0, resident_bulk = 0;  // CTAs per SM, computed once
   static int sms = 0;
   if (resident == 0) {
@@ -783,7 +808,7 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
                                (int)cudaSharedmemCarveoutMaxShared);
       if (e != cudaSuccess) return e;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &resident_bulk, codec_u8_tma_kernel<R, kStages>, kThreads, kSmem);
+          &resident_bulk, codec_u8_tma_kernel<R, kStages>, kRingThreads, kSmem);
       if (e != cudaSuccess) return e;
       if (resident_bulk < 1) resident_bulk = 1;
     }
@@ -792,13 +817,14 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
   int per_sm = bulk ? resident_bulk : resident;
   if (cp.ctas_per_sm > 0 && cp.ctas_per_sm < per_sm) per_sm = cp.ctas_per_sm;
   int64_t grid = (int64_t)per_sm * sms;
-  const int64_t by_work = (tab.total_units + kThreads / 32 - 1) / (kThreads / 32);
+  const int threads = bulk ? kRingThreads : kThreads;
+  const int64_t by_work = (tab.total_units + threads / 32 - 1) / (threads / 32);
   if (by_work < grid) grid = by_work;
   if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   if (grid < 1) grid = 1;
   if constexpr (DT == 0) {
     if (bulk) {
-      codec_u8_tma_kernel<R, kStages><<<(unsigned)grid, kThreads, kSmem, s>>>(tab, cp, sse);
+      codec_u8_tma_kernel<R, kStages><<<(unsigned)grid, kRingThreads, kSmem, s>>>(tab, cp, sse);
       return cudaGetLastError();
     }
   }

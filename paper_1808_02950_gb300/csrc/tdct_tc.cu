@@ -332,6 +332,263 @@ __global__ void __launch_bounds__(kTcThreads, TDCT_TC_MINB)
   }
 }
 
+// Software-pipelined variant: the MMA of tile t + 1 runs while tile t is
+// computed.  Per iteration: wait for MMA(t) and read its accumulator (the A
+// tile is then free), convert the prefetched rows of tile t + 1 into A,
+// issue MMA(t + 1) into the other accumulator, then compute tile t, reading
+// its pixels again from global memory (an L2 hit: they were fetched by the
+// prefetch one tile earlier) instead of holding them in registers across
+// the MMA.  Two tensor-memory accumulators of N columns, one mbarrier each.
+template <int R>
+__global__ void __launch_bounds__(kTcThreads, TDCT_TC_MINB)
+    codec_u8_tc_pipe_kernel(const PlaneTable tab, const CodecParams cp,
+                            const uint16_t* __restrict__ b_global,
+                            unsigned long long* __restrict__ sse_out) {
+  constexpr int NH = nh_of(R);
+  constexpr int N = 2 * NH;
+  constexpr int COLS = tmem_cols_of(2 * N);
+  constexpr int B_BYTES = NH * 128;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* a_tile = smem;
+  uint8_t* raw_all = smem + kATileBytes;  // [warp][8 rows x 512 B]
+  uint8_t* b_mat = raw_all + 4 * kUnitBytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(b_mat + B_BYTES);  // [0,1] mma, [2..5] raw
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 6);
+
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t* raw = raw_all + wid * kUnitBytes;  // this warp's rows of the next tile
+  const uint32_t bar_raw = smem_addr(bar + 2 + wid);
+
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"((uint32_t)COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 6; ++i) mbar_init(smem_addr(bar + i), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int e = threadIdx.x; e < B_BYTES / 16; e += kTcThreads)
+    reinterpret_cast<uint4*>(b_mat)[e] = __ldg(reinterpret_cast<const uint4*>(b_global) + e);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t trow = tmem + ((uint32_t)(wid * 32) << 16);
+  const uint32_t a0 = smem_addr(a_tile), b0 = smem_addr(b_mat);
+  constexpr uint32_t idesc = idesc_f16(128, NH);
+
+  const int64_t tiles = (tab.total_units + 3) / 4;
+  const int64_t t_begin = (tiles * blockIdx.x) / gridDim.x;
+  const int64_t t_end = (tiles * (blockIdx.x + 1)) / gridDim.x;
+
+  // prefetch cursor: this warp's unit of a tile -> its rows into its raw slot
+  int64_t pf_end = -1, pf_ubegin = 0, pf_pitch = 0;
+  const uint8_t* pf_img = nullptr;
+  int pf_W = 0, pf_chunks = 1;
+  uint32_t raw_phase = 0;
+  auto prefetch = [&](int64_t t) -> bool {
+    const int64_t u = t * 4 + wid;
+    if (t >= t_end || u >= tab.total_units) return false;
+    if (u >= pf_end) {
+      const int q = find_plane(tab, u);
+      const PlaneDesc& Q = tab.d ? tab.d[q] : tab.one;
+      pf_img = Q.img;
+      pf_pitch = Q.pitch;
+      pf_W = Q.W;
+      pf_chunks = Q.chunks;
+      pf_ubegin = Q.unit_begin;
+      pf_end = (q + 1 < tab.n) ? tab.d[q + 1].unit_begin : tab.total_units;
+    }
+    const int64_t local = u - pf_ubegin;
+    const int by = (int)(local / pf_chunks);
+    const int chunk = (int)(local - (int64_t)by * pf_chunks);
+    const uint32_t row_bytes = (uint32_t)min(512, pf_W - chunk * 512);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (lane == 0) mbar_arrive_expect_tx(bar_raw, 8u * row_bytes);
+    __syncwarp();
+    if (lane < 8) {
+      const uint8_t* src = pf_img + (int64_t)(by * 8 + lane) * pf_pitch + (int64_t)chunk * 512;
+      bulk_copy_g2s(smem_addr(raw + lane * 512), src, row_bytes, bar_raw);
+    }
+    return true;
+  };
+
+  // Convert the rows in `raw` (the next tile) into A (bounded wait).
+  bool in_flight = false;
+  auto stage_tile = [&]() -> bool {
+    bool ok = true;
+    if (in_flight) {
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar_raw, raw_phase, cp.wait_limit));
+      raw_phase ^= 1u;
+      in_flight = false;
+    }
+    uint4 rw[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) rw[k] = *reinterpret_cast<const uint4*>(raw + k * 512 + lane * 16);
+    __syncwarp();
+    uint8_t* arow = a_tile + (wid * 32 + lane) * 16;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint4 lo = make_uint4(biased_f16x2(rw[k].x, 0x4140u), biased_f16x2(rw[k].x, 0x4342u),
+                                  biased_f16x2(rw[k].y, 0x4140u), biased_f16x2(rw[k].y, 0x4342u));
+      const uint4 hi = make_uint4(biased_f16x2(rw[k].z, 0x4140u), biased_f16x2(rw[k].z, 0x4342u),
+                                  biased_f16x2(rw[k].w, 0x4140u), biased_f16x2(rw[k].w, 0x4342u));
+      *reinterpret_cast<uint4*>(arow + (2 * k) * 2048) = lo;
+      *reinterpret_cast<uint4*>(arow + (2 * k + 1) * 2048) = hi;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    return ok;
+  };
+  auto issue_mma = [&](int buf, bool hook) {
+    if (threadIdx.x == 0 && !hook) {
+      tc_fence_after();
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint64_t ad = smem_desc(a0 + (4 * q + h) * 2048, 4096, 128);
+          const uint64_t bd = smem_desc(b0 + q * 2 * (NH * 16), NH * 16, 128);
+          mma_f16(tmem + buf * N + h * NH, ad, bd, idesc, q > 0 ? 1u : 0u);
+        }
+      mma_commit(smem_addr(bar + buf));
+    }
+  };
+
+  uint32_t mma_phase = 0;  // bit b: parity of accumulator b's next completion
+  bool mma_pending[2] = {false, false};
+  bool alive = t_begin < t_end;
+  if (alive) {
+    in_flight = prefetch(t_begin);
+    bool ok = stage_tile();
+    if (ok) in_flight = prefetch(t_begin + 1);
+    tc_fence_before();
+    alive = __syncthreads_and(ok);
+    if (alive) {
+      issue_mma(0, cp.test_hook == 1 && blockIdx.x == 0);
+      mma_pending[0] = true;
+    } else if (threadIdx.x == 0 && cp.status) {
+      atomicExch(cp.status, 4 /* TDCT_ETIMEOUT */);
+    }
+  }
+
+  int p = -1;
+  int64_t p_end = -1;
+  PlaneDesc P;
+  unsigned long long acc = 0;
+  for (int64_t t = t_begin; t < t_end && alive; ++t) {
+    const int b = (int)((t - t_begin) & 1);
+    // accumulator of tile t
+    // warp-uniform: stage_tile below contains warp-collective operations
+    bool ok = __all_sync(0xffffffffu,
+                         mbar_wait_bounded(smem_addr(bar + b), (mma_phase >> b) & 1u, cp.wait_limit));
+    mma_phase ^= 1u << b;
+    mma_pending[b] = false;
+    tc_fence_after();
+    uint32_t zf[2][NH];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int g = 0; g < NH / 8; ++g) tmem_ld8(trow + b * N + h * NH + 8 * g, zf[h] + 8 * g);
+    tmem_wait_ld();
+    // A is free: stage tile t + 1 and start its MMA before computing tile t
+    const bool more = t + 1 < t_end;
+    if (more && ok) {
+      ok = stage_tile();
+      if (ok) in_flight = prefetch(t + 2);
+    }
+    tc_fence_before();
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0 && cp.status) atomicExch(cp.status, 4 /* TDCT_ETIMEOUT */);
+      alive = false;
+      break;
+    }
+    if (more) {
+      issue_mma(b ^ 1, false);
+      mma_pending[b ^ 1] = true;
+    }
+    // compute tile t
+    const int64_t u = t * 4 + wid;
+    if (u < tab.total_units) {
+      if (u >= p_end) {
+        if (p >= 0) {
+          acc = warp_sum_u64(acc);
+          if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+          acc = 0;
+        }
+        p = find_plane(tab, u);
+        P = tab.d ? tab.d[p] : tab.one;
+        p_end = (p + 1 < tab.n) ? tab.d[p + 1].unit_begin : tab.total_units;
+      }
+      const int64_t local = u - P.unit_begin;
+      const int by = (int)(local / P.chunks);
+      const int chunk = (int)(local - (int64_t)by * P.chunks);
+      const int bx0 = chunk * 64 + 2 * lane;
+      if (bx0 < P.nbx) {
+        const uint8_t* src = P.img + (int64_t)(by * 8) * P.pitch + (int64_t)bx0 * 8;
+        uint2 xa[8], xb[8];
+        uint32_t sse = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + k * P.pitch));
+          xa[k] = make_uint2(v.x, v.y);
+          xb[k] = make_uint2(v.z, v.w);
+          sse = __dp4a(xa[k].x, xa[k].x, sse);
+          sse = __dp4a(xa[k].y, xa[k].y, sse);
+          sse = __dp4a(xb[k].x, xb[k].x, sse);
+          sse = __dp4a(xb[k].y, xb[k].y, sse);
+        }
+        const bool store = P.recon != nullptr;
+        const int64_t rp = P.recon_pitch;
+        uint2* out0 = store ? reinterpret_cast<uint2*>(P.recon + (int64_t)(by * 8) * rp +
+                                                       (int64_t)bx0 * 8)
+                            : nullptr;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t w[64];
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int pz = 8 * i + j;
+              if (kept(R, i, j)) {
+                int32_t z = __float2int_rn(__uint_as_float(zf[h][zz_index(i, j)]));
+                if (pz == 0) z -= 65536;  // the 1024 bias of the 64 pixels
+                w[pz] = (uint32_t)z * (uint32_t)(2 * cp.cmul[pz]);
+              } else {
+                w[pz] = 0u;
+              }
+            }
+          w[0] += kL2;
+          sse += inverse_epilogue_u8<R>(w, h == 0 ? xa : xb, store ? out0 + h : nullptr, rp,
+                                        store, true, 8, 8);
+        }
+        acc += sse;
+      }
+    }
+  }
+  // drain: copies and MMAs still in flight (bounded) before the memory goes
+  if (in_flight) mbar_wait_bounded(bar_raw, raw_phase, cp.wait_limit);
+  for (int b = 0; b < 2; ++b)
+    if (mma_pending[b]) mbar_wait_bounded(smem_addr(bar + b), (mma_phase >> b) & 1u, cp.wait_limit);
+  if (p >= 0) {
+    acc = warp_sum_u64(acc);
+    if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (wid == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)COLS)
+                 : "memory");
+  }
+}
+
 // B matrices for every r: slot r - 1 holds [row k (8)][coefficient n (NH)]
 // [column l (8) fp16] = (t_i kron t_j)[k][l] for the n-th kept zig-zag
 // position (i, j) (zero for n >= r), NH = nh(class(r)); written once per
@@ -401,27 +658,30 @@ cudaError_t tc_prepare(const uint16_t** table) {
 template <int R>
 cudaError_t launch_codec_tc(const PlaneTable& tab, const CodecParams& cp, int r_exact,
                             unsigned long long* sse, cudaStream_t s) {
-  constexpr int N = 2 * nh_of(R);
+  constexpr int N = 4 * nh_of(R);  // accumulator columns of the pipelined variant (the larger)
 #ifndef TDCT_TC_SMEM_PAD
 #define TDCT_TC_SMEM_PAD 0
 #endif
   constexpr size_t kSmem =
-      kATileBytes + 4 * kUnitBytes + (size_t)nh_of(R) * 128 + 64 + TDCT_TC_SMEM_PAD;
+      kATileBytes + 4 * kUnitBytes + (size_t)nh_of(R) * 128 + 128 + TDCT_TC_SMEM_PAD;
   // at most 512 / COLS CTAs may hold tensor memory on one SM at a time
   constexpr int kMaxPerSm = 512 / tmem_cols_of(N);
-  static int resident = 0, sms = 0;
+  // variant 1: software-pipelined (wins at large r); 0: one tile at a time
+  const bool pipe = cp.tc_variant == 1;
+  auto kernel = pipe ? codec_u8_tc_pipe_kernel<R> : codec_u8_tc_kernel<R>;
+  static int resident_v[2] = {0, 0}, sms = 0;
+  int& resident = resident_v[pipe ? 1 : 0];
   if (resident == 0) {
-    cudaError_t e = cudaFuncSetAttribute(codec_u8_tc_kernel<R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(codec_u8_tc_kernel<R>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     // residency from registers and shared memory (the occupancy query
     // under-reports kernels that hold tensor memory)
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, codec_u8_tc_kernel<R>);
+    e = cudaFuncGetAttributes(&fa, kernel);
     if (e != cudaSuccess) return e;
     int dev = 0, regs_sm = 65536, smem_sm = 233472, reserved = 1024;
     if (cudaGetDevice(&dev) == cudaSuccess) {
@@ -448,7 +708,7 @@ cudaError_t launch_codec_tc(const PlaneTable& tab, const CodecParams& cp, int r_
   if (tiles < 1) return cudaSuccess;
   int64_t grid = (int64_t)per_sm * sms;
   if (grid > tiles) grid = tiles;
-  codec_u8_tc_kernel<R><<<(unsigned)grid, kTcThreads, kSmem, s>>>(tab, cp, bmat, sse);
+  kernel<<<(unsigned)grid, kTcThreads, kSmem, s>>>(tab, cp, bmat, sse);
   return cudaGetLastError();
 }
 

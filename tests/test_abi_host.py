@@ -106,6 +106,8 @@ def test_batched_rejects():
         == _lib.TDCT_EINVAL
     assert L.tdct_codec_error_batched(ctypes.addressof(planes), 1, tb, nb, FAKE, None, 9, None) \
         == _lib.TDCT_EUNSUPPORTED
+    assert L.tdct_codec_error_batched(ctypes.addressof(planes), 1, tb, nb, FAKE, None, -1, None) \
+        == _lib.TDCT_EUNSUPPORTED
     h = ctypes.c_void_p()
     planes = P.make_planes_raw([(FAKE, 64, 16, 64, 10, 3, 0, 0)])
     assert L.tdct_plan_create(ctypes.addressof(planes), 1, tb, nb, 0, ctypes.byref(h)) \

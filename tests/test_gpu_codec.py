@@ -287,17 +287,19 @@ def _run_batch_path(views, rs, path, with_recon=True):
     return sse.cpu().numpy(), psnr.cpu().numpy(), recons
 
 
+@pytest.mark.parametrize("path", ["tensor", "tensor_pipelined"])
 @pytest.mark.parametrize("H,W", [(8, 16), (16, 512), (64, 1040), (48, 2048), (8, 4096)])
-def test_tensor_path_matches_oracle(H, W):
+def test_tensor_path_matches_oracle(H, W, path):
+    path = P.TDCT_PATH_TENSOR if path == "tensor" else P.TDCT_PATH_TENSOR_PIPELINED
     rng = np.random.default_rng(H * 11 + W)
     host = rng.integers(0, 256, (H, W)).astype(np.uint8)
     img = torch.from_numpy(host).to(DEV)
     for r in (1, 3, 8, 9, 10, 16, 17, 32, 33, 64):
-        sse, psnr, recons = _run_batch_path([img], [r], P.TDCT_PATH_TENSOR)
+        sse, psnr, recons = _run_batch_path([img], [r], path)
         want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
         assert sse[0] == want_sse, f"r={r}"
         assert np.array_equal(recons[0].cpu().numpy(), want_rec), f"r={r}"
-        sse2, _, _ = _run_batch_path([img], [r], P.TDCT_PATH_TENSOR, with_recon=False)
+        sse2, _, _ = _run_batch_path([img], [r], path, with_recon=False)
         assert sse2[0] == want_sse
 
 
@@ -320,9 +322,11 @@ def test_tensor_path_equals_butterfly_on_many_images():
     views = [imgs[i] for i in range(64)]
     a, pa, ra = _run_batch_path(views, [r] * 64, P.TDCT_PATH_TENSOR)
     b, pb, rb = _run_batch_path(views, [r] * 64, P.TDCT_PATH_BUTTERFLY)
+    c, pc, rc = _run_batch_path(views, [r] * 64, P.TDCT_PATH_TENSOR_PIPELINED)
     assert np.array_equal(a, b) and np.array_equal(pa, pb)
+    assert np.array_equal(c, b) and np.array_equal(pc, pb)
     for i in (0, 31, 63):
-        assert torch.equal(ra[i], rb[i])
+        assert torch.equal(ra[i], rb[i]) and torch.equal(rc[i], rb[i])
     assert a[0] == oc.codec_plane(imgs[0].cpu().numpy(), M.T1, r, want_recon=False)[0]
     planes = P.make_planes(views, [r] * 64)
     plan = P.tdct_plan_create(planes, path=P.TDCT_PATH_TENSOR)
@@ -334,16 +338,18 @@ def test_tensor_path_equals_butterfly_on_many_images():
     plan.close()
 
 
-def test_tensor_path_bounded_wait_timeout():
+@pytest.mark.parametrize("variant", ["tensor", "tensor_pipelined"])
+def test_tensor_path_bounded_wait_timeout(variant):
+    path = P.TDCT_PATH_TENSOR if variant == "tensor" else P.TDCT_PATH_TENSOR_PIPELINED
     img = torch.from_numpy(np.random.default_rng(3).integers(0, 256, (64, 1024)).astype(np.uint8)).to(DEV)
     P.tdct_sync_status()
-    _run_batch_path([img], [16], P.TDCT_PATH_TENSOR)  # tables built, kernel loaded
+    _run_batch_path([img], [16], path)  # tables built, kernel loaded
     P.tdct_debug_inject_wait_timeout(True)
-    _run_batch_path([img], [16], P.TDCT_PATH_TENSOR)
+    _run_batch_path([img], [16], path)
     with pytest.raises(P.TdctError) as e:
         P.tdct_sync_status()
     assert e.value.code == 4
-    sse, _, recons = _run_batch_path([img], [16], P.TDCT_PATH_TENSOR)
+    sse, _, recons = _run_batch_path([img], [16], path)
     want_sse, want_rec, _ = oc.codec_plane(img.cpu().numpy(), M.T1, 16)
     assert sse[0] == want_sse and np.array_equal(recons[0].cpu().numpy(), want_rec)
     P.tdct_sync_status()
