@@ -196,30 +196,49 @@ cudaError_t dispatch_codec(int r, int dtype, const PlaneTable& tab, unsigned lon
 
 // ---- forward / inverse only kernels ------------------------------------------
 
+// Forward only: one block per thread; the 32 blocks of a warp are staged in
+// shared memory so that the warp writes its 8 KB of coefficients as
+// contiguous 16-byte stores (blocks are consecutive in the output).
 template <int DT>
 __global__ void __launch_bounds__(128) forward_kernel(const PlaneDesc P, int32_t* __restrict__ coef,
                                                       int coef_vec) {
+  __shared__ __align__(16) int32_t stage[4][32 * 68];  // 68-word block stride: bank skew
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* st = stage[wid];
   const int64_t nb = (int64_t)P.nbx * P.nby;
-  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb;
-       b += (int64_t)gridDim.x * blockDim.x) {
-    const int by = (int)(b / P.nbx), bx = (int)(b - (int64_t)by * P.nbx);
-    const bool interior = (by * 8 + 8 <= P.H) && ((bx + 1) * 8 <= P.W) && (P.vec16 & 1);
-    RowWords<DT> rw;
-    load_block<DT>(P, by, bx, interior, rw);
-    uint32_t x[64], z[64];
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + wid * 32); base < nb; base += step) {
+    const int64_t b = base + lane;
+    if (b < nb) {
+      const int by = (int)(b / P.nbx), bx = (int)(b - (int64_t)by * P.nbx);
+      const bool interior = (by * 8 + 8 <= P.H) && ((bx + 1) * 8 <= P.W) && (P.vec16 & 1);
+      RowWords<DT> rw;
+      load_block<DT>(P, by, bx, interior, rw);
+      uint32_t x[64], z[64];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) unpack_row<DT>(rw, k, x + 8 * k);
-    fwd2d<uint32_t>(x, z);
-    int32_t* dst = coef + b * 64;
-    if (coef_vec) {
+      for (int k = 0; k < 8; ++k) unpack_row<DT>(rw, k, x + 8 * k);
+      fwd2d<uint32_t>(x, z);
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        reinterpret_cast<int4*>(dst)[i] =
+        *reinterpret_cast<int4*>(st + lane * 68 + 4 * i) =
             make_int4((int)z[4 * i], (int)z[4 * i + 1], (int)z[4 * i + 2], (int)z[4 * i + 3]);
-    } else {
-#pragma unroll
-      for (int p = 0; p < 64; ++p) dst[p] = (int32_t)z[p];
     }
+    __syncwarp();
+    const int64_t nblk = min((int64_t)32, nb - base);
+    int32_t* dst = coef + base * 64;
+    if (coef_vec) {
+      for (int e = lane; e < nblk * 16; e += 32) {
+        const int blk = e >> 4, i = e & 15;
+        reinterpret_cast<int4*>(dst)[e] =
+            *reinterpret_cast<const int4*>(st + blk * 68 + 4 * i);
+      }
+    } else {
+      for (int e = lane; e < nblk * 64; e += 32) {
+        const int blk = e >> 6, i = e & 63;
+        dst[e] = st[blk * 68 + i];
+      }
+    }
+    __syncwarp();
   }
 }
 
