@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--path", default="auto",
                     choices=["butterfly", "tensor", "tensor_pipelined", "auto"],
                     help="forward-transform engine of the fused codec (auto: the plan autotunes)")
+    ap.add_argument("--transform", default="T1", choices=["T1", "T2", "RDCT", "T6", "T4", "LOx2"],
+                    help="the 8-point matrix (T1: fused kernels; others: generic kernels)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -248,7 +250,10 @@ def time_ours(args, dist, out):
     import torch
 
     import paper_1808_02950_gb300 as P
+    from paper_1808_02950_gb300 import transforms
 
+    T = transforms.NAMED[args.transform]
+    Tn = dict(T=T, n=transforms.row_norms(T))
     dev = f"cuda:{dist.local_rank}"
     torch.cuda.set_device(dev)
     wl = Workload(args.workload, dev, args.images)
@@ -258,7 +263,7 @@ def time_ours(args, dist, out):
     psnr = torch.zeros(n, dtype=torch.float64, device=dev)
     path = {"butterfly": P.TDCT_PATH_BUTTERFLY, "tensor": P.TDCT_PATH_TENSOR,
             "tensor_pipelined": P.TDCT_PATH_TENSOR_PIPELINED, "auto": P.TDCT_PATH_AUTO}[args.path]
-    plan = P.tdct_plan_create(planes, path=path)
+    plan = P.tdct_plan_create(planes, path=path, **Tn)
     plan_cfg = plan.config()
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -288,12 +293,15 @@ def time_ours(args, dist, out):
     kernel_ms = statistics.mean(per_step)
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (kernel_ms / 1e3) / 1e9
-    traffic, traffic_src = profiled_traffic(wl.blocks) if args.workload == "batch_1024x1024" else (None, None)
+    traffic, traffic_src = (profiled_traffic(wl.blocks)
+                            if args.workload == "batch_1024x1024" and args.transform == "T1"
+                            else (None, None))
     out.update({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32 (u8 in/out)", "data": "synthetic",
-        "config": {**wl.desc, "parallelism": f"replicas{dist.world}", "path": plan_cfg["path"],
+        "config": {**wl.desc, "transform": args.transform,
+                   "parallelism": f"replicas{dist.world}", "path": plan_cfg["path"],
                    "ctas_per_sm": plan_cfg["ctas_per_sm"], "autotuned": args.path == "auto",
                    "l2": "inputs larger than L2 (no flush)" if algo_bytes > 256e6 else
                    "inputs smaller than L2"},
@@ -321,7 +329,7 @@ def time_ours(args, dist, out):
                                        path={"butterfly": P.TDCT_PATH_BUTTERFLY,
                                              "tensor": P.TDCT_PATH_TENSOR,
                                              "tensor_pipelined": P.TDCT_PATH_TENSOR_PIPELINED}[
-                                                 plan_cfg["path"]])
+                                                 plan_cfg["path"]], **Tn)
             sse_h.copy_(sse, non_blocking=True)
             psnr_h.copy_(psnr, non_blocking=True)
 
@@ -347,15 +355,21 @@ def time_ours(args, dist, out):
     return wl
 
 
-def cpu_oracle_rate(planes_host, budget_s: float):
+def oracle_matrix(name: str):
+    from oracle import matrices as M
+
+    return (2 * M.T_LO).astype("int64") if name == "LOx2" else M.NAMED[name]
+
+
+def cpu_oracle_rate(planes_host, budget_s: float, transform: str = "T1"):
     """Run the oracle over host planes with one thread per core until the
     budget is spent; returns (blocks/s, blocks done, threads, planes done)."""
     from concurrent.futures import ThreadPoolExecutor
 
     from oracle import codec as oc
-    from oracle import matrices as M
 
     oc.lib()
+    T = oracle_matrix(transform)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     done_blocks = 0
@@ -372,7 +386,7 @@ def cpu_oracle_rate(planes_host, budget_s: float):
                 i = idx[0]
                 idx[0] += 1
             img, r = planes_host[i]
-            oc.codec_plane(img, M.T1, r)
+            oc.codec_plane(img, T, r)
             nb = ((img.shape[0] + 7) // 8) * ((img.shape[1] + 7) // 8)
             with lock:
                 done_blocks += nb
@@ -405,7 +419,7 @@ def main():
     wl = time_ours(args, dist, out)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         sample = host_sample(wl, 256)
-        rate, nb, cores, npl = cpu_oracle_rate(sample, args.cpu_seconds)
+        rate, nb, cores, npl = cpu_oracle_rate(sample, args.cpu_seconds, args.transform)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{npl} of {len(wl.planes)} planes ({nb} blocks), "
                                          f"C oracle (int64 definition), one thread per core"}
@@ -429,11 +443,11 @@ def main_reference(args):
     sample = host_sample(wl, 64)
     per_step_budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_oracle_rate(sample, per_step_budget)
+        cpu_oracle_rate(sample, per_step_budget, args.transform)
     rates, blocks, cores, planes = [], 0, 1, 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        rate, nb, cores, npl = cpu_oracle_rate(sample, per_step_budget)
+        rate, nb, cores, npl = cpu_oracle_rate(sample, per_step_budget, args.transform)
         rates.append(rate)
         blocks += nb
         planes += npl
@@ -443,7 +457,8 @@ def main_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": {**wl.desc, "parallelism": "host cores"},
+        "data": "synthetic",
+        "config": {**wl.desc, "transform": args.transform, "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{planes} plane runs over {len(sample)} sampled planes, "
                                    f"{per_step_budget:.1f} s budget per step"},

@@ -15,9 +15,14 @@
  *   - T is the 8x8 low-complexity matrix, row-major int8 (row k = t_k^T,
  *     §3.1 Eq. (4)); n are the 8 squared row norms, n_k = (T T^T)_kk, i.e.
  *     S = diag(1/sqrt(n_k)) as §4.1 states it for T1.  The library checks
- *     that T T^T == diag(n) and returns TDCT_ENOTORTHO otherwise.  The fused
- *     GPU path implements the paper's T1 (§4.1, fast algorithm of §5.1);
- *     another orthogonal T returns TDCT_EUNSUPPORTED.
+ *     that T T^T == diag(n) with every n_k >= 1 and returns TDCT_ENOTORTHO
+ *     otherwise.  The paper's T1 (§4.1) runs on the fused kernels of its
+ *     fast algorithm (§5.1), on either engine below.  Any other orthogonal
+ *     T (T2 of §4.1, the orthogonal matrices of Table 2, ...) runs on the
+ *     generic kernels (direct integer products with T, CUDA cores only)
+ *     with the same exact results, provided L = lcm(n) <= 725 (the exact
+ *     32-bit range: 4082 L^2 < 2^31); a larger L returns
+ *     TDCT_EUNSUPPORTED, and so does a tensor-core path with T != T1.
  *   - Planes are row-major with a row pitch in BYTES.  dtype TDCT_U8 holds
  *     8-bit samples (images), TDCT_I16 holds int16 residual samples in
  *     [-255, 255].  H and W are in samples and need not be multiples of 8:
@@ -63,7 +68,8 @@ enum tdct_precision { TDCT_FP32 = 0, TDCT_BF16 = 1 };
 
 /*
  * Forward-transform engines of the fused codec.
- *   TDCT_PATH_BUTTERFLY  the fast algorithm of §5.1 on the CUDA cores.
+ *   TDCT_PATH_BUTTERFLY  the fast algorithm of §5.1 on the CUDA cores
+ *                        (for T != T1: the generic kernels).
  *   TDCT_PATH_TENSOR     Z = T1 X T1^T as a GEMM on the tensor cores
  *                        (tcgen05.mma; sm_103a has no int8 MMA, so pixels
  *                        enter as exact fp16 values and the FP32 accumulation

@@ -24,6 +24,7 @@
 #include "../../include/tdct.h"
 #include "tdct_classes.h"
 #include "tdct_dct.h"
+#include "tdct_generic.cuh"
 #include "tdct_kernels.cuh"
 #include "tdct_tc.h"
 
@@ -65,8 +66,36 @@ constexpr int8_t kT1[64] = {
     1, 2, 1,  0,  -2, -2, 2,  2,  0, -1, 1,  -1, -1, 1,  1,  -1, -1, 1, 2,  -2, 0,  1,
     -1, 0, 2, -2, 1,  -2, 2,  -1, -1, 2, -2, 1,  0,  -1, 2,  -2, 2,  -2, 1, 0};
 
-// T T^T == diag(n) (Eq. (2) with a diagonal S), and T == T1 for the fused path.
-int check_transform(const int8_t* T, const int32_t* n) {
+// The transform of a call.  T1 runs on the fused kernels (fast algorithm of
+// §5.1, both engines); any other orthogonal T on the generic kernels, whose
+// parameters are built here.
+struct Transform {
+  bool t1 = true;
+  GenericParams base;  // T, L^2 and the rounding division constant; cmul2 per r
+  int32_t q[8];        // q_k = L / n_k
+};
+
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) {
+    const int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// T T^T == diag(n) (Eq. (2) with a diagonal S); builds the generic parameters
+// when T is not T1.
+//
+// Bounds of the generic kernels.  A reconstructed sample is the orthogonal
+// projection of the block onto the kept basis functions, so |N / L^2| <=
+// ||block||_2 <= 8 * 255 = 2040 for u8 and int16 planes; the kernels form 2N
+// in wrapping 32-bit arithmetic, exact when |2N| + L^2 < 2^31, i.e.
+// 4082 L^2 < 2^31 (L <= 725).  Rounding divides a = |2N| + L^2 (or 2N + L^2)
+// by 2 L^2 as (a * magic) >> (32 + shift) with magic = ceil(2^k / (2 L^2)) <
+// 2^31; with e = magic * 2 L^2 - 2^k the quotient is exact for 0 <= a < A when
+// e * A < 2^k, and it is checked here for A = 4082 L^2.
+int resolve_transform(const int8_t* T, const int32_t* n, Transform* tr) {
   if (!T || !n) return fail(TDCT_EINVAL, "T and n must not be NULL");
   for (int a = 0; a < 8; ++a)
     for (int b = 0; b < 8; ++b) {
@@ -77,10 +106,52 @@ int check_transform(const int8_t* T, const int32_t* n) {
         return fail(TDCT_ENOTORTHO, "(T T^T)[%d][%d] = %lld but diag(n) gives %lld", a, b,
                     (long long)dot, (long long)want);
     }
-  if (std::memcmp(T, kT1, 64) != 0)
+  for (int k = 0; k < 8; ++k)
+    if (n[k] < 1) return fail(TDCT_ENOTORTHO, "row %d of T is zero (n_%d = 0)", k, k);
+  tr->t1 = std::memcmp(T, kT1, 64) == 0;
+  if (tr->t1) return TDCT_OK;
+  int64_t L = 1;
+  for (int k = 0; k < 8; ++k) {
+    L = L / gcd64(L, n[k]) * n[k];
+    if (L > 725)
+      return fail(TDCT_EUNSUPPORTED,
+                  "lcm of the row norms n exceeds 725: the exact 32-bit reconstruction needs "
+                  "4082 L^2 < 2^31");
+  }
+  const int64_t L2 = L * L, d = 2 * L2, A = 4082 * L2;
+  int k = 32;
+  while (k < 62 && (((int64_t)1 << (k + 1)) + d - 1) / d < ((int64_t)1 << 31)) ++k;
+  const int64_t magic = (((int64_t)1 << k) + d - 1) / d;
+  const int64_t e = magic * d - ((int64_t)1 << k);
+  if (magic >= ((int64_t)1 << 31) || (unsigned __int128)e * (unsigned __int128)A >=
+                                         ((unsigned __int128)1 << k))
+    return fail(TDCT_EUNSUPPORTED, "no exact 32-bit division constant for L = %lld",
+                (long long)L);
+  std::memset(&tr->base, 0, sizeof tr->base);
+  for (int i = 0; i < 64; ++i) tr->base.T[i] = T[i];
+  tr->base.L2 = (int32_t)L2;
+  tr->base.magic = (int32_t)magic;
+  tr->base.shift = k - 32;
+  for (int i = 0; i < 8; ++i) tr->q[i] = (int32_t)(L / n[i]);
+  return TDCT_OK;
+}
+
+// Generic parameters for retention r: cmul2 = 2 q_i q_j on the first r
+// zig-zag positions (Eq. (11) mask), else 0.
+GenericParams generic_for_r(const Transform& tr, int r) {
+  GenericParams gp = tr.base;
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) gp.cmul2[8 * i + j] = kept(r, i, j) ? 2 * tr.q[i] * tr.q[j] : 0;
+  return gp;
+}
+
+int check_engine(const Transform& tr, int path) {
+  if (path < TDCT_PATH_AUTO || path > TDCT_PATH_TENSOR_PIPELINED)
+    return fail(TDCT_EUNSUPPORTED, "path %d is not a tdct_path", path);
+  if (!tr.t1 && (path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED))
     return fail(TDCT_EUNSUPPORTED,
-                "the fused GPU path implements T1 (its fast algorithm); other orthogonal T are "
-                "not implemented");
+                "the tensor-core engine implements T1 only; use TDCT_PATH_AUTO or "
+                "TDCT_PATH_BUTTERFLY for another T");
   return TDCT_OK;
 }
 
@@ -170,6 +241,21 @@ cudaError_t dispatch_codec_tc(int r, const PlaneTable& tab, unsigned long long* 
 #define TDCT_CASE(R) \
   case R:            \
     return launch_codec_tc<R>(tab, cp, r, sse, s);
+    TDCT_FOR_EACH_CLASS(TDCT_CASE)
+#undef TDCT_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t dispatch_codec_generic(int r, int dtype, const PlaneTable& tab, const Transform& tr,
+                                   unsigned long long* sse, cudaStream_t s) {
+  const GenericParams gp = generic_for_r(tr, r);
+  switch (r_class(r)) {
+#define TDCT_CASE(R)                                                          \
+  case R:                                                                     \
+    return dtype == TDCT_U8 ? launch_codec_generic<R, 0>(tab, gp, sse, s)     \
+                            : launch_codec_generic<R, 1>(tab, gp, sse, s);
     TDCT_FOR_EACH_CLASS(TDCT_CASE)
 #undef TDCT_CASE
     default:
@@ -343,10 +429,10 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
 }
 
 // Enqueue the kernels of a batch whose descriptors live at d_descs (device).
-cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_descs,
-                          const int64_t* d_npix, int nplanes, unsigned long long* sse,
-                          double* psnr, cudaStream_t s, int path = TDCT_PATH_AUTO,
-                          int ctas_per_sm = 0, int tc_variant = 0) {
+cudaError_t enqueue_batch(const Transform& tr, const std::vector<Group>& groups,
+                          const PlaneDesc* d_descs, const int64_t* d_npix, int nplanes,
+                          unsigned long long* sse, double* psnr, cudaStream_t s,
+                          int path = TDCT_PATH_AUTO, int ctas_per_sm = 0, int tc_variant = 0) {
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long) * nplanes, s);
   if (e != cudaSuccess) return e;
   for (const Group& g : groups) {
@@ -357,7 +443,9 @@ cudaError_t enqueue_batch(const std::vector<Group>& groups, const PlaneDesc* d_d
     tab.total_units = g.units;
     tab.any_bulk = g.any_bulk;
     const bool tensor = path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED;
-    if (tensor && g.any_bulk && g.dtype == TDCT_U8)
+    if (!tr.t1)
+      e = dispatch_codec_generic(g.r, g.dtype, tab, tr, sse, s);
+    else if (tensor && g.any_bulk && g.dtype == TDCT_U8)
       e = dispatch_codec_tc(g.r, tab, sse, s, ctas_per_sm,
                             path == TDCT_PATH_TENSOR_PIPELINED ? 1 : tc_variant);
     else
@@ -379,6 +467,7 @@ using namespace tdct;
 // ---- plans ----------------------------------------------------------------------
 
 struct tdct_plan {
+  Transform tr;
   std::vector<Group> groups;
   int path = TDCT_PATH_AUTO;   // engine used by launches (never AUTO after creation)
   int ctas_per_sm = 0;         // launch shape (0 = the library default)
@@ -428,8 +517,8 @@ int autotune_plan(tdct_plan* plan) {
     for (int it = 0; it < 5 && e == cudaSuccess; ++it) {
       if (it >= 2) e = cudaEventRecord(ev0, s);
       if (e == cudaSuccess)
-        e = enqueue_batch(plan->groups, plan->d_descs, plan->d_npix, plan->nplanes, sse, nullptr,
-                          s, c.path, c.cps, c.variant);
+        e = enqueue_batch(plan->tr, plan->groups, plan->d_descs, plan->d_npix, plan->nplanes, sse,
+                          nullptr, s, c.path, c.cps, c.variant);
       if (e == cudaSuccess && it >= 2) e = cudaEventRecord(ev1, s);
       if (e == cudaSuccess && it >= 2) e = cudaEventSynchronize(ev1);
       if (e == cudaSuccess && it >= 2) e = cudaEventElapsedTime(&t[it - 2], ev0, ev1);
@@ -465,7 +554,8 @@ const char* tdct_version(void) { return "tdct 0.1 (sm_103a)"; }
 
 int tdct_forward(const void* d_img, int64_t pitch, int H, int W, int dtype, const int8_t T[64],
                  const int32_t n[8], int32_t* d_coef, tdct_stream_t stream) {
-  int rc = check_transform(T, n);
+  Transform tr;
+  int rc = resolve_transform(T, n, &tr);
   if (rc) return rc;
   if ((rc = check_plane(d_img, pitch, H, W, dtype, "tdct_forward"))) return rc;
   if (!d_coef || (reinterpret_cast<uintptr_t>(d_coef) & 3))
@@ -474,6 +564,10 @@ int tdct_forward(const void* d_img, int64_t pitch, int H, int W, int dtype, cons
   const int vec = (reinterpret_cast<uintptr_t>(d_coef) & 15) == 0;
   const int grid = grid_for((int64_t)P.nbx * P.nby, 128);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!tr.t1) {
+    const cudaError_t eg = launch_forward_generic(P, generic_for_r(tr, 64), d_coef, s, grid);
+    return eg == cudaSuccess ? TDCT_OK : cuda_fail(eg, "tdct_forward launch");
+  }
   if (dtype == TDCT_U8) forward_kernel<0><<<grid, 128, 0, s>>>(P, d_coef, vec);
   else forward_kernel<1><<<grid, 128, 0, s>>>(P, d_coef, vec);
   const cudaError_t e = cudaGetLastError();
@@ -483,7 +577,8 @@ int tdct_forward(const void* d_img, int64_t pitch, int H, int W, int dtype, cons
 int tdct_zonal_inverse(const int32_t* d_coef, int H, int W, int dtype, const int8_t T[64],
                        const int32_t n[8], int r, void* d_out, int64_t out_pitch,
                        tdct_stream_t stream) {
-  int rc = check_transform(T, n);
+  Transform tr;
+  int rc = resolve_transform(T, n, &tr);
   if (rc) return rc;
   if ((rc = check_r(r))) return rc;
   if ((rc = check_plane(d_out, out_pitch, H, W, dtype, "tdct_zonal_inverse"))) return rc;
@@ -492,8 +587,12 @@ int tdct_zonal_inverse(const int32_t* d_coef, int H, int W, int dtype, const int
   const PlaneDesc P = make_desc(d_out, out_pitch, H, W, dtype, r, d_out, out_pitch, 0);
   const int vec = (reinterpret_cast<uintptr_t>(d_coef) & 15) == 0;
   const int grid = grid_for((int64_t)P.nbx * P.nby, 128);
-  const CodecParams cp = make_params(r);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!tr.t1) {
+    const cudaError_t eg = launch_inverse_generic(d_coef, P, generic_for_r(tr, r), s, grid);
+    return eg == cudaSuccess ? TDCT_OK : cuda_fail(eg, "tdct_zonal_inverse launch");
+  }
+  const CodecParams cp = make_params(r);
   if (dtype == TDCT_U8) inverse_kernel<0><<<grid, 128, 0, s>>>(d_coef, P, cp, vec);
   else inverse_kernel<1><<<grid, 128, 0, s>>>(d_coef, P, cp, vec);
   const cudaError_t e = cudaGetLastError();
@@ -504,7 +603,8 @@ int tdct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype,
                      const int8_t T[64], const int32_t n[8], int r, void* d_recon,
                      int64_t recon_pitch, uint64_t* d_sse, double* d_psnr,
                      tdct_stream_t stream) {
-  int rc = check_transform(T, n);
+  Transform tr;
+  int rc = resolve_transform(T, n, &tr);
   if (rc) return rc;
   if ((rc = check_r(r))) return rc;
   if ((rc = check_plane(d_img, pitch, H, W, dtype, "tdct_codec_error"))) return rc;
@@ -524,8 +624,9 @@ int tdct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype,
   unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error memset");
-  if ((e = dispatch_codec(r, dtype, tab, sse, 0, s)) != cudaSuccess)
-    return cuda_fail(e, "tdct_codec_error launch");
+  e = tr.t1 ? dispatch_codec(r, dtype, tab, sse, 0, s)
+            : dispatch_codec_generic(r, dtype, tab, tr, sse, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error launch");
   if (d_psnr) {
     psnr_kernel<<<1, 32, 0, s>>>(sse, nullptr, (int64_t)H * W, d_psnr, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "psnr launch");
@@ -536,10 +637,10 @@ int tdct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype,
 int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t T[64],
                              const int32_t n[8], uint64_t* d_sse, double* d_psnr, int path,
                              tdct_stream_t stream) {
-  int rc = check_transform(T, n);
+  Transform tr;
+  int rc = resolve_transform(T, n, &tr);
   if (rc) return rc;
-  if (path < TDCT_PATH_AUTO || path > TDCT_PATH_TENSOR_PIPELINED)
-    return fail(TDCT_EUNSUPPORTED, "path %d is not a tdct_path", path);
+  if ((rc = check_engine(tr, path))) return rc;
   if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
     return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
   std::vector<PlaneDesc> descs;
@@ -564,7 +665,7 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
           cudaSuccess &&
       (e = cudaMemcpyAsync(d_npix, npix.data(), bytes_npix, cudaMemcpyHostToDevice, s)) ==
           cudaSuccess)
-    e = enqueue_batch(groups, d_descs, d_npix, nplanes,
+    e = enqueue_batch(tr, groups, d_descs, d_npix, nplanes,
                       reinterpret_cast<unsigned long long*>(d_sse), d_psnr, s, path);
   const cudaError_t ef = cudaFreeAsync(scratch, s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error_batched");
@@ -576,14 +677,15 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
                      const int32_t n[8], int path, tdct_plan** out_plan) {
   if (!out_plan) return fail(TDCT_EINVAL, "out_plan is NULL");
   *out_plan = nullptr;
-  int rc = check_transform(T, n);
+  Transform tr;
+  int rc = resolve_transform(T, n, &tr);
   if (rc) return rc;
-  if (path < TDCT_PATH_AUTO || path > TDCT_PATH_TENSOR_PIPELINED)
-    return fail(TDCT_EUNSUPPORTED, "path %d is not a tdct_path", path);
+  if ((rc = check_engine(tr, path))) return rc;
   std::vector<PlaneDesc> descs;
   std::vector<int64_t> npix;
   tdct_plan* plan = new (std::nothrow) tdct_plan;
   if (!plan) return fail(TDCT_ENOMEM, "host allocation failed");
+  plan->tr = tr;
   if ((rc = build_batch(planes, nplanes, descs, plan->groups, npix))) {
     delete plan;
     return rc;
@@ -616,7 +718,8 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
   }
   if (path == TDCT_PATH_AUTO) {
     plan->path = TDCT_PATH_BUTTERFLY;
-    if ((rc = autotune_plan(plan))) {
+    // another T has one engine (the generic kernels): nothing to tune
+    if (tr.t1 && (rc = autotune_plan(plan))) {
       tdct_plan_destroy(plan);
       return rc;
     }
@@ -652,7 +755,7 @@ int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stre
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    const cudaError_t ee = enqueue_batch(plan->groups, plan->d_descs, plan->d_npix,
+    const cudaError_t ee = enqueue_batch(plan->tr, plan->groups, plan->d_descs, plan->d_npix,
                                          plan->nplanes, sse, d_psnr, plan->capture_stream,
                                          plan->path, plan->ctas_per_sm, plan->tc_variant);
     e = cudaStreamEndCapture(plan->capture_stream, &graph);
@@ -722,7 +825,8 @@ extern "C" {
 int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, const int8_t T[64],
                                      const int32_t n[8], uint64_t* d_sse, double* d_psnr,
                                      tdct_stream_t stream) {
-  int rc = check_transform(T, n);
+  Transform tr;
+  int rc = resolve_transform(T, n, &tr);
   if (rc) return rc;
   if (nplanes > TDCT_NOALLOC_MAX_PLANES)
     return fail(TDCT_EINVAL,
@@ -746,7 +850,7 @@ int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, cons
     e = cudaMemcpyAsync(d_npix, npix.data(), sizeof(int64_t) * npix.size(),
                         cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = enqueue_batch(groups, d_descs, d_npix, nplanes,
+    e = enqueue_batch(tr, groups, d_descs, d_npix, nplanes,
                       reinterpret_cast<unsigned long long*>(d_sse), d_psnr, s);
   return e == cudaSuccess ? TDCT_OK : cuda_fail(e, "tdct_codec_error_batched_noalloc");
 }

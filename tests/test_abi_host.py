@@ -69,12 +69,55 @@ def test_codec_error_rejects(kw, code):
     assert msg
 
 
-def test_other_orthogonal_T_is_unsupported_not_wrong():
-    T2 = [[1, 1, 1, 1, 1, 1, 1, 1], [2, 1, 2, 0, 0, -2, -1, -2], [2, 1, -1, -2, -2, -1, 1, 2],
-          [2, 0, -2, -1, 1, 2, 0, -2], [1, -1, -1, 1, 1, -1, -1, 1], [1, -2, 0, 2, -2, 0, 2, -1],
-          [1, -2, 2, -1, -1, 2, -2, 1], [0, -2, 1, -2, 2, -1, 2, 0]]
-    rc, msg = _call_codec(T=T2, n=(8, 18, 20, 18, 8, 18, 20, 18))
-    assert rc == _lib.TDCT_EUNSUPPORTED, msg
+T2 = [[1, 1, 1, 1, 1, 1, 1, 1], [2, 1, 2, 0, 0, -2, -1, -2], [2, 1, -1, -2, -2, -1, 1, 2],
+      [2, 0, -2, -1, 1, 2, 0, -2], [1, -1, -1, 1, 1, -1, -1, 1], [1, -2, 0, 2, -2, 0, 2, -1],
+      [1, -2, 2, -1, -1, 2, -2, 1], [0, -2, 1, -2, 2, -1, 2, 0]]
+N2 = (8, 18, 20, 18, 8, 18, 20, 18)
+
+
+def test_other_orthogonal_T_passes_the_transform_checks():
+    # T2 (§4.1) is accepted: the call gets as far as the plane checks
+    rc, msg = _call_codec(T=T2, n=N2, img=None)
+    assert rc == _lib.TDCT_EINVAL and "NULL plane" in msg, msg
+
+
+def test_non_orthogonal_and_degenerate_T_rejected():
+    # the BAS-2008 matrix of Table 2 as printed is not orthogonal: T T^T has
+    # off-diagonal entries, so no diagonal S exists (Eq. (2))
+    bas = [[1, 1, 1, 1, 1, 1, 1, 1], [1, 1, 1, 0, 0, -1, -1, -1], [1, 1, -1, -1, -1, -1, 1, 1],
+           [1, 0, -1, 0, 0, 1, 0, -1], [1, -1, -1, 1, 1, -1, -1, 1], [1, -1, 1, 0, 0, -1, 1, -1],
+           [1, -1, 1, -1, -1, 1, -1, 1], [1, -1, 1, -1, 1, -1, 1, -1]]
+    rc, msg = _call_codec(T=bas, n=(8, 6, 8, 4, 8, 6, 8, 8))
+    assert rc == _lib.TDCT_ENOTORTHO, msg
+    zero_row = [list(r) for r in T2]
+    zero_row[7] = [0] * 8
+    rc, msg = _call_codec(T=zero_row, n=N2[:7] + (0,))
+    assert rc == _lib.TDCT_ENOTORTHO and "zero" in msg, msg
+
+
+def test_T_beyond_the_exact_32_bit_range_is_unsupported():
+    # Walsh-Hadamard rows scaled by 1, 3, 5, 7: orthogonal, n = 8 c^2, and
+    # lcm(n) = 8 * 9 * 25 * 49 > 725, outside the exact 32-bit reconstruction
+    H = [[1]]
+    for _ in range(3):
+        H = [row + row for row in H] + [row + [-v for v in row] for row in H]
+    c = [1, 3, 5, 7, 1, 3, 5, 7]
+    T = [[c[k] * v for v in H[k]] for k in range(8)]
+    rc, msg = _call_codec(T=T, n=tuple(8 * ck * ck for ck in c))
+    assert rc == _lib.TDCT_EUNSUPPORTED and "lcm" in msg, msg
+
+
+def test_tensor_engine_rejects_other_T():
+    L = P.load()
+    tb, nb = _lib._T_n(T2, N2)
+    planes = P.make_planes_raw([(FAKE, 64, 16, 64, 10, 0, 0, 0)])
+    for path in (_lib.TDCT_PATH_TENSOR, _lib.TDCT_PATH_TENSOR_PIPELINED):
+        assert L.tdct_codec_error_batched(ctypes.addressof(planes), 1, tb, nb, FAKE, None, path,
+                                          None) == _lib.TDCT_EUNSUPPORTED
+        h = ctypes.c_void_p()
+        assert L.tdct_plan_create(ctypes.addressof(planes), 1, tb, nb, path, ctypes.byref(h)) \
+            == _lib.TDCT_EUNSUPPORTED
+        assert not h.value
 
 
 def test_forward_and_inverse_reject():
@@ -123,3 +166,20 @@ def test_errors_raise_in_binding():
     with pytest.raises(P.TdctError) as e:
         P.tdct_codec_error(img, 0, sse)
     assert e.value.code == _lib.TDCT_EINVAL
+
+
+def test_named_transforms_agree_with_the_oracle_copies():
+    """The library's table of named matrices and the oracle's, typed
+    independently from §4.1 and Table 2, agree (LO enters scaled by 2)."""
+    import numpy as np
+
+    from oracle import matrices as M
+    from paper_1808_02950_gb300 import transforms as tr
+
+    want = {"T1": M.T1, "T2": M.T2, "RDCT": M.T_RDCT, "T6": M.T6, "T4": M.T4,
+            "LOx2": 2 * M.T_LO}
+    assert set(tr.NAMED) == set(want)
+    for name, T in tr.NAMED.items():
+        assert np.array_equal(np.array(T), want[name]), name
+        assert tr.row_norms(T) == tuple(int(v) for v in np.einsum("ij,ij->i", want[name], want[name]))
+    assert tr.T1 == tuple(tuple(r) for r in P.T1)
