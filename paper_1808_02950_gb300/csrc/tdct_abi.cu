@@ -192,7 +192,10 @@ CodecParams make_params(int r, int ctas_per_sm = 0, int tc_variant = 0) {
   CodecParams cp;
   std::memset(&cp, 0, sizeof cp);
   for (int i = 0; i < 8; ++i)
-    for (int j = 0; j < 8; ++j) cp.cmul[8 * i + j] = kept(r, i, j) ? q_of(i) * q_of(j) : 0;
+    for (int j = 0; j < 8; ++j) {
+      cp.cmul[8 * i + j] = kept(r, i, j) ? q_of(i) * q_of(j) : 0;
+      cp.cmul2[8 * i + j] = 2 * cp.cmul[8 * i + j];
+    }
   cp.status = status_word();
   cp.wait_limit = 2000000000ll;  // about a second of SM clock
   cp.ctas_per_sm = ctas_per_sm;
@@ -493,7 +496,7 @@ int autotune_plan(tdct_plan* plan) {
   bool any_u8_bulk = false;
   for (const Group& g : plan->groups) any_u8_bulk |= (g.any_bulk && g.dtype == TDCT_U8);
   struct Cand { int path, cps, variant; };
-  std::vector<Cand> cands = {{TDCT_PATH_BUTTERFLY, 0, 0}, {TDCT_PATH_BUTTERFLY, 1, 0}};
+  std::vector<Cand> cands = {{TDCT_PATH_BUTTERFLY, 0, 0}, {TDCT_PATH_BUTTERFLY, 2, 0}};
   if (any_u8_bulk) {
     const uint16_t* table = nullptr;
     if (tc_prepare(&table) == cudaSuccess) {

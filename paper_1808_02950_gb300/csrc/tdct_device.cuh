@@ -33,6 +33,25 @@ __host__ __device__ constexpr int zz_index(int i, int j) {
 // Retention mask M_r of §6.1: position (i, j) kept iff its scan index < r.
 __host__ __device__ constexpr bool kept(int r, int i, int j) { return zz_index(i, j) < r; }
 
+// Rows (vertical frequencies i) and columns (horizontal frequencies j) that
+// hold a kept position: 1 + the largest such index.  A separable pass along
+// one direction only has to form the outputs inside the other's extent, so
+// the cheaper pass order follows from these.
+__host__ __device__ constexpr int kept_rows(int r) {
+  int e = 0;
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j)
+      if (kept(r, i, j) && i + 1 > e) e = i + 1;
+  return e;
+}
+__host__ __device__ constexpr int kept_cols(int r) {
+  int e = 0;
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j)
+      if (kept(r, i, j) && j + 1 > e) e = j + 1;
+  return e;
+}
+
 // ---- T1 constants ---------------------------------------------------------
 // q = L / n with n = diag(T1 T1^T) = (8,18,20,18,8,18,20,18), L = lcm(n) = 360.
 __host__ __device__ constexpr int q_of(int i) {

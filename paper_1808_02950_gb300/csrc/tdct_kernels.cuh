@@ -148,9 +148,11 @@ __device__ __forceinline__ void reconstruct(uint32_t w[64], int32_t out[64]) {
 
 // Per-launch constants: cmul[8 i + j] = q_i q_j if position (i, j) is among
 // the first r zig-zag positions, else 0 (the zonal mask M_r with S^2 folded
-// in, §6.1).  Lives in the kernel parameter (constant) bank.
+// in, §6.1); cmul2 = 2 cmul (the doubled multipliers of the u8 paths).  Lives
+// in the kernel parameter (constant) bank.
 struct CodecParams {
   int32_t cmul[64];
+  int32_t cmul2[64];
   int* status;           // device status word (TDCT_ETIMEOUT on a bounded wait giving up)
   long long wait_limit;  // clock cycles a bulk-copy wait may take before giving up
   int32_t test_hook;     // 1: the first copy of warp 0 is never issued (timeout test)
@@ -349,20 +351,22 @@ __device__ __forceinline__ uint32_t min_relu_s16x2(uint32_t a, uint32_t b) {
   return d;
 }
 
-// Lanes (block A, block B) of the 8 samples of one row pair.
+// Lanes (block A, block B) of the 8 samples of one row pair: p[l] = a_l +
+// 65536 b_l.  a02 = [a0, 0, a2, 0] supplies both a sample and a zero byte, so
+// each p[l] is one more byte permute with the row word of block B
+// (12 permutes per row pair).
 __device__ __forceinline__ void pair_row(uint2 a, uint2 b, uint32_t p[8]) {
   const uint32_t a02 = __byte_perm(a.x, 0u, 0x4240u), a13 = __byte_perm(a.x, 0u, 0x4341u);
-  const uint32_t b02 = __byte_perm(b.x, 0u, 0x4240u), b13 = __byte_perm(b.x, 0u, 0x4341u);
   const uint32_t a46 = __byte_perm(a.y, 0u, 0x4240u), a57 = __byte_perm(a.y, 0u, 0x4341u);
-  const uint32_t b46 = __byte_perm(b.y, 0u, 0x4240u), b57 = __byte_perm(b.y, 0u, 0x4341u);
-  p[0] = __byte_perm(a02, b02, 0x5410u);
-  p[2] = __byte_perm(a02, b02, 0x7632u);
-  p[1] = __byte_perm(a13, b13, 0x5410u);
-  p[3] = __byte_perm(a13, b13, 0x7632u);
-  p[4] = __byte_perm(a46, b46, 0x5410u);
-  p[6] = __byte_perm(a46, b46, 0x7632u);
-  p[5] = __byte_perm(a57, b57, 0x5410u);
-  p[7] = __byte_perm(a57, b57, 0x7632u);
+  // selectors: bytes 0-3 from the a-word, 4-7 from the b-word
+  p[0] = __byte_perm(a02, b.x, 0x1410u);
+  p[2] = __byte_perm(a02, b.x, 0x1612u);
+  p[1] = __byte_perm(a13, b.x, 0x1510u);
+  p[3] = __byte_perm(a13, b.x, 0x1712u);
+  p[4] = __byte_perm(a46, b.y, 0x1410u);
+  p[6] = __byte_perm(a46, b.y, 0x1612u);
+  p[5] = __byte_perm(a57, b.y, 0x1510u);
+  p[7] = __byte_perm(a57, b.y, 0x1712u);
 }
 
 __device__ __forceinline__ int32_t lane_lo(uint32_t v) { return (int32_t)(int16_t)(v & 0xffffu); }
@@ -443,6 +447,104 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8(const uint32_t w[64], co
   return acc;
 }
 
+// The inverse with rows first: r[i][l] = sum_j w[i][j] t_j[l] for the kept
+// rows only, then each column l: 2N[k][l] + L^2 = sum_i t_i[k] r[i][l] over
+// the kept rows.  The dense second pass then has kept_rows(R) inputs instead
+// of kept_cols(R); it yields columns, so the rounded samples are packed per
+// column pair and the row bytes assembled after columns 0-3 and 4-7.  It
+// holds more values live than the row-streaming order, so it is used only
+// where it removes a dense 8-input pass (policy 1, measured): kept set
+// spanning all 8 columns but not all 8 rows.  Policy 0: never; 2: whenever
+// kept_rows(R) < kept_cols(R).
+#ifndef TDCT_INV_ROWS_FIRST
+#define TDCT_INV_ROWS_FIRST 1
+#endif
+
+template <int R>
+__host__ __device__ constexpr bool inverse_rows_first() {
+  return TDCT_INV_ROWS_FIRST == 2   ? kept_rows(R) < kept_cols(R)
+         : TDCT_INV_ROWS_FIRST == 1 ? (kept_cols(R) == 8 && kept_rows(R) < 8)
+                                    : false;
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t inverse_epilogue_u8_rows(const uint32_t w[64], const uint2 x[8],
+                                                             uint2* __restrict__ out_row0,
+                                                             int64_t out_pitch, bool store,
+                                                             bool full, int valid_rows,
+                                                             int valid_cols) {
+  uint32_t rr[64];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) inv8<uint32_t>(w + 8 * i, rr + 8 * i);
+  uint32_t yw[2][8];  // packed row bytes: yw[0][k] = samples 0-3 of row k, yw[1][k] = 4-7
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t c[2][8];  // clamped s16x2 pairs of columns (4 half + 2 m, +1) per row
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int l = 4 * half + 2 * m;
+      uint32_t ca[8], cb[8], na[8], nb[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        ca[i] = rr[8 * i + l];
+        cb[i] = rr[8 * i + l + 1];
+      }
+      inv8<uint32_t>(ca, na);
+      inv8<uint32_t>(cb, nb);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t ha = (uint32_t)__mulhi((int32_t)na[k], kDivMagic);
+        const uint32_t hb = (uint32_t)__mulhi((int32_t)nb[k], kDivMagic);
+        c[m][k] = min_relu_s16x2(__byte_perm(ha, hb, 0x7632u), 0x00ff00ffu);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) yw[half][k] = __byte_perm(c[0][k], c[1][k], 0x6420u);
+  }
+  uint32_t acc = 0;
+  const uint64_t colmask = valid_cols >= 8 ? ~0ull : ((1ull << (8 * valid_cols)) - 1ull);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    uint2 y = make_uint2(yw[0][k], yw[1][k]);
+    if (!full) {
+      const uint64_t m = k < valid_rows ? colmask : 0ull;
+      y.x &= (uint32_t)m;
+      y.y &= (uint32_t)(m >> 32);
+    }
+    acc = __dp4a(y.x, y.x, acc);
+    acc = __dp4a(y.y, y.y, acc);
+    acc -= 2u * __dp4a(x[k].x, y.x, __dp4a(x[k].y, y.y, 0u));
+    if (store && full) out_row0[(int64_t)k * (out_pitch >> 3)] = y;
+    if (store && !full && k < valid_rows) {
+      uint8_t* row = reinterpret_cast<uint8_t*>(out_row0) + (int64_t)k * out_pitch;
+#pragma unroll
+      for (int l = 0; l < 8; ++l)
+        if (l < valid_cols) row[l] = (uint8_t)((l < 4 ? y.x >> (8 * l) : y.y >> (8 * (l - 4))) & 0xffu);
+    }
+  }
+  return acc;
+}
+
+// Inverse pass order for class R (inverse_rows_first).
+template <int R>
+__device__ __forceinline__ uint32_t inverse_epilogue_u8_any(const uint32_t w[64], const uint2 x[8],
+                                                            uint2* __restrict__ out_row0,
+                                                            int64_t out_pitch, bool store,
+                                                            bool full, int valid_rows,
+                                                            int valid_cols) {
+  if constexpr (inverse_rows_first<R>())
+    return inverse_epilogue_u8_rows<R>(w, x, out_row0, out_pitch, store, full, valid_rows,
+                                       valid_cols);
+  else
+    return inverse_epilogue_u8<R>(w, x, out_row0, out_pitch, store, full, valid_rows, valid_cols);
+}
+
+// Forward pass order when the kept set is as wide as tall: 1 rows first,
+// 0 columns first.
+#ifndef TDCT_FWD_ROWS_FIRST_ON_TIE
+#define TDCT_FWD_ROWS_FIRST_ON_TIE 1
+#endif
+
 // Both blocks of a lane (samples already in registers, zero outside the
 // plane) through the packed forward and the per-block inverse.
 // FULL: the caller guarantees both blocks exist, lie inside the plane and
@@ -465,24 +567,40 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
     sse = __dp4a(xb[k].x, xb[k].x, sse);
     sse = __dp4a(xb[k].y, xb[k].y, sse);
   }
-  // packed forward: rows, then columns
+  // packed forward.  The first pass forms, for each of the 8 rows (or
+  // columns), only the outputs inside the kept columns (rows); the second
+  // only the kept positions.  Rows first when the kept set is no wider than
+  // tall, columns first otherwise (fewer first-pass outputs).
   uint32_t z[64];
   {
+    uint32_t pk[64];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) pair_row(xa[k], xb[k], pk + 8 * k);
     uint32_t t[64];
+    if constexpr (TDCT_FWD_ROWS_FIRST_ON_TIE ? kept_cols(R) <= kept_rows(R) : kept_cols(R) < kept_rows(R)) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      uint32_t p[8];
-      pair_row(xa[k], xb[k], p);
-      fwd8<uint32_t>(p, t + 8 * k);
-    }
+      for (int k = 0; k < 8; ++k) fwd8<uint32_t>(pk + 8 * k, t + 8 * k);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      uint32_t col[8], o[8];
+      for (int j = 0; j < 8; ++j) {
+        uint32_t col[8], o[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) col[k] = t[8 * k + j];
-      fwd8<uint32_t>(col, o);
+        for (int k = 0; k < 8; ++k) col[k] = t[8 * k + j];
+        fwd8<uint32_t>(col, o);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) z[8 * i + j] = o[i];
+        for (int i = 0; i < 8; ++i) z[8 * i + j] = o[i];
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        uint32_t col[8], o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) col[k] = pk[8 * k + l];
+        fwd8<uint32_t>(col, o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[8 * i + l] = o[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) fwd8<uint32_t>(t + 8 * i, z + 8 * i);
     }
   }
   const bool store = P.recon != nullptr;
@@ -500,7 +618,7 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
         const int p = 8 * i + j;
         if (kept(R, i, j)) {
           const int32_t zz = b == 0 ? lane_lo(z[p]) : lane_hi(z[p]);
-          w[p] = (uint32_t)zz * (uint32_t)(2 * cp.cmul[p]);
+          w[p] = (uint32_t)zz * (uint32_t)cp.cmul2[p];
         } else {
           w[p] = 0u;
         }
@@ -511,11 +629,11 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
     uint2* o = store ? (b == 0 ? out0 : out0 + 1) : nullptr;
     if (!FULL && store && !fast_store) {
       // unaligned recon or edge block: byte stores of valid samples
-      sse += inverse_epilogue_u8<R>(w, b == 0 ? xa : xb, o, rp, true, false, valid_rows,
-                                    b == 0 ? vc0 : vc1);
+      sse += inverse_epilogue_u8_any<R>(w, b == 0 ? xa : xb, o, rp, true, false, valid_rows,
+                                        b == 0 ? vc0 : vc1);
     } else {
-      sse += inverse_epilogue_u8<R>(w, b == 0 ? xa : xb, o, rp, store, full, valid_rows,
-                                    b == 0 ? vc0 : vc1);
+      sse += inverse_epilogue_u8_any<R>(w, b == 0 ? xa : xb, o, rp, store, full, valid_rows,
+                                        b == 0 ? vc0 : vc1);
     }
   }
   return sse;
@@ -558,6 +676,7 @@ __global__ void __launch_bounds__(256, DT == 0 ? TDCT_U8_MINB : 1) codec_kernel(
   int p = -1;
   int64_t p_end = -1;
   PlaneDesc P;  // current plane, held in registers
+  int next_by = 0, next_chunk = 0;  // unit cursor inside the plane
   unsigned long long acc = 0;
   for (int64_t u = u_begin; u < u_end; ++u) {
     if (u >= p_end) {
@@ -569,11 +688,16 @@ __global__ void __launch_bounds__(256, DT == 0 ? TDCT_U8_MINB : 1) codec_kernel(
       p = find_plane(tab, u);
       P = tab.d ? tab.d[p] : tab.one;
       p_end = (p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U;
+      const int64_t local = u - P.unit_begin;
+      next_by = (int)(local / P.chunks);
+      next_chunk = (int)(local - (int64_t)next_by * P.chunks);
+    }
+    const int by = next_by, chunk = next_chunk;
+    if (++next_chunk == P.chunks) {
+      next_chunk = 0;
+      ++next_by;
     }
     if (P.dtype != DT) continue;  // never true for tables the host builds
-    const int64_t local = u - P.unit_begin;
-    const int by = (int)(local / P.chunks);
-    const int chunk = (int)(local - (int64_t)by * P.chunks);
     if constexpr (DT == 0) acc += codec_lane_u8<R>(P, by, chunk * 64 + 2 * lane, cp);
     else acc += codec_lane<R, DT>(P, by, chunk * 64 + 2 * lane, cp);
   }
@@ -645,15 +769,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 
 // Threads per CTA of the bulk-copy ring kernel and the resident CTAs per SM
 // it is compiled for (registers <= 65536 / (threads * CTAs)).
+// 4 warps x 3 CTAs per SM leave 168 registers per thread, enough for the
+// unrolled two-block codec of the classes up to 32 (measured faster than
+// 8 warps x 2 CTAs at 128 registers); the classes from 36 up need more live
+// values and run faster at 2 CTAs (255 registers) than spilling at 3.
 #ifndef TDCT_RING_THREADS
-#define TDCT_RING_THREADS 256
-#endif
-#ifndef TDCT_RING_MINB
-#define TDCT_RING_MINB (512 / TDCT_RING_THREADS)
+#define TDCT_RING_THREADS 128
 #endif
 
+template <int R>
+__host__ __device__ constexpr int ring_min_blocks() {
+#ifdef TDCT_RING_MINB
+  return TDCT_RING_MINB;
+#else
+  return R >= 36 ? 2 : 3;
+#endif
+}
+
 template <int R, int STAGES>
-__global__ void __launch_bounds__(TDCT_RING_THREADS, TDCT_RING_MINB)
+__global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
     codec_u8_tma_kernel(const PlaneTable tab, const CodecParams cp,
                         unsigned long long* __restrict__ sse_out) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -675,17 +809,20 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, TDCT_RING_MINB)
   const int64_t u_begin = (U * warp) / nwarps;
   const int64_t u_end = (U * (warp + 1)) / nwarps;
 
-  // producer cursor: the fields of the plane of the next unit to prefetch
-  int64_t pp_end = -1, pp_ubegin = 0, pp_pitch = 0;
+  // producer cursor: the plane of the next unit to prefetch and the unit's
+  // (block-row, chunk) within it, advanced incrementally (a division only
+  // when the cursor enters a plane)
+  int64_t pp_end = -1, pp_pitch = 0;
   const uint8_t* pp_img = nullptr;
-  int pp_W = 0, pp_chunks = 1;
+  int pp_W = 0, pp_chunks = 1, pp_by = 0, pp_chunk = 0, pp_s = 0;
   uint32_t issued = 0;  // bit s: slot s holds a copy in flight
   uint32_t phase = 0;   // bit s: parity of slot s's next completion
   int64_t u_pf = u_begin;
 
   auto issue_next = [&]() {
     const int64_t u = u_pf++;
-    const int s = (int)((u - u_begin) % STAGES);
+    const int s = pp_s;
+    pp_s = pp_s + 1 == STAGES ? 0 : pp_s + 1;
     if (u >= pp_end) {
       const int q = find_plane(tab, u);
       const PlaneDesc& Q = tab.d ? tab.d[q] : tab.one;
@@ -693,12 +830,16 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, TDCT_RING_MINB)
       pp_pitch = Q.pitch;
       pp_W = Q.W;
       pp_chunks = Q.chunks;
-      pp_ubegin = Q.unit_begin;
       pp_end = (q + 1 < tab.n) ? tab.d[q + 1].unit_begin : U;
+      const int64_t local = u - Q.unit_begin;
+      pp_by = (int)(local / pp_chunks);
+      pp_chunk = (int)(local - (int64_t)pp_by * pp_chunks);
     }
-    const int64_t local = u - pp_ubegin;
-    const int by = (int)(local / pp_chunks);
-    const int chunk = (int)(local - (int64_t)by * pp_chunks);
+    const int by = pp_by, chunk = pp_chunk;
+    if (++pp_chunk == pp_chunks) {
+      pp_chunk = 0;
+      ++pp_by;
+    }
     const uint32_t row_bytes = (uint32_t)min(512, pp_W - chunk * 512);
     const uint32_t bar = bars + 8 * s;
     // order this warp's earlier generic reads of the slot before the async writes
@@ -734,6 +875,7 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, TDCT_RING_MINB)
   int p = -1;
   int64_t p_end = -1;
   PlaneDesc P;
+  int by = 0, chunk = 0, s = 0;  // consumer cursor, advanced like the producer's
   unsigned long long acc = 0;
   for (int64_t u = u_begin; u < u_end; ++u) {
     if (u >= p_end) {
@@ -745,15 +887,20 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, TDCT_RING_MINB)
       p = find_plane(tab, u);
       P = tab.d ? tab.d[p] : tab.one;
       p_end = (p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U;
+      const int64_t local = u - P.unit_begin;
+      by = (int)(local / P.chunks);
+      chunk = (int)(local - (int64_t)by * P.chunks);
     }
-    const int64_t local = u - P.unit_begin;
-    const int by = (int)(local / P.chunks);
-    const int chunk = (int)(local - (int64_t)by * P.chunks);
     const int bx0 = chunk * 64 + 2 * lane;
-    const int s = (int)((u - u_begin) % STAGES);
-    if (!wait_slot(s)) return;
+    const int cur_by = by, cur_s = s;
+    if (++chunk == P.chunks) {
+      chunk = 0;
+      ++by;
+    }
+    s = s + 1 == STAGES ? 0 : s + 1;
+    if (!wait_slot(cur_s)) return;
     uint2 xa[8], xb[8];
-    const uint8_t* slot = ring + s * kUnitBytes + lane * 16;
+    const uint8_t* slot = ring + cur_s * kUnitBytes + lane * 16;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const uint4 v = *reinterpret_cast<const uint4*>(slot + k * 512);
@@ -762,7 +909,7 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, TDCT_RING_MINB)
     }
     __syncwarp();
     if (u_pf < u_end) issue_next();  // refill the slot just read
-    if (bx0 < P.nbx) acc += codec_pair_u8<R, true>(P, by, bx0, xa, xb, cp);
+    if (bx0 < P.nbx) acc += codec_pair_u8<R, true>(P, cur_by, bx0, xa, xb, cp);
   }
   if (p >= 0) {
     acc = warp_sum_u64(acc);
@@ -770,7 +917,7 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, TDCT_RING_MINB)
   }
 }
 
-// Slots per warp of the bulk-copy ring (2 CTAs x 8 warps x 3 x 4 KB fit 228 KB).
+// Slots per warp of the bulk-copy ring (3 CTAs x 4 warps x 3 x 4 KB = 144 KB per SM).
 #ifndef TDCT_U8_STAGES
 #define TDCT_U8_STAGES 3
 #endif

@@ -100,12 +100,21 @@ __device__ __forceinline__ uint32_t biased_f16x2(uint32_t w, uint32_t sel) {
   return __byte_perm(w, 0x64646464u, sel);
 }
 
-#ifndef TDCT_TC_MINB
-#define TDCT_TC_MINB 4
+// CTAs per SM each tensor kernel is compiled for (128 or 168 registers per
+// thread; measured): the one-tile kernel keeps 4 up to class 16, the
+// pipelined kernel and the larger classes run faster without spills at 3.
+// The launcher derives the actual residency from the compiled kernel.
+template <int R, bool PIPE>
+__host__ __device__ constexpr int tc_min_blocks() {
+#ifdef TDCT_TC_MINB
+  return TDCT_TC_MINB;
+#else
+  return (PIPE || R > 16) ? 3 : 4;
 #endif
+}
 
 template <int R>
-__global__ void __launch_bounds__(kTcThreads, TDCT_TC_MINB)
+__global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, false>())
     codec_u8_tc_kernel(const PlaneTable tab, const CodecParams cp,
                        const uint16_t* __restrict__ b_global,
                        unsigned long long* __restrict__ sse_out) {
@@ -304,13 +313,13 @@ __global__ void __launch_bounds__(kTcThreads, TDCT_TC_MINB)
             if (kept(R, i, j)) {
               int32_t z = __float2int_rn(__uint_as_float(zf[b][zz_index(i, j)]));
               if (pz == 0) z -= 65536;  // the 1024 bias of the 64 pixels
-              w[pz] = (uint32_t)z * (uint32_t)(2 * cp.cmul[pz]);
+              w[pz] = (uint32_t)z * (uint32_t)cp.cmul2[pz];
             } else {
               w[pz] = 0u;
             }
           }
         w[0] += kL2;
-        sse += inverse_epilogue_u8<R>(w, b == 0 ? xa : xb, store ? out0 + b : nullptr, rp, store,
+        sse += inverse_epilogue_u8_any<R>(w, b == 0 ? xa : xb, store ? out0 + b : nullptr, rp, store,
                                       true, 8, 8);
       }
       acc += sse;
@@ -340,7 +349,7 @@ __global__ void __launch_bounds__(kTcThreads, TDCT_TC_MINB)
 // prefetch one tile earlier) instead of holding them in registers across
 // the MMA.  Two tensor-memory accumulators of N columns, one mbarrier each.
 template <int R>
-__global__ void __launch_bounds__(kTcThreads, TDCT_TC_MINB)
+__global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, true>())
     codec_u8_tc_pipe_kernel(const PlaneTable tab, const CodecParams cp,
                             const uint16_t* __restrict__ b_global,
                             unsigned long long* __restrict__ sse_out) {
@@ -558,13 +567,13 @@ __global__ void __launch_bounds__(kTcThreads, TDCT_TC_MINB)
               if (kept(R, i, j)) {
                 int32_t z = __float2int_rn(__uint_as_float(zf[h][zz_index(i, j)]));
                 if (pz == 0) z -= 65536;  // the 1024 bias of the 64 pixels
-                w[pz] = (uint32_t)z * (uint32_t)(2 * cp.cmul[pz]);
+                w[pz] = (uint32_t)z * (uint32_t)cp.cmul2[pz];
               } else {
                 w[pz] = 0u;
               }
             }
           w[0] += kL2;
-          sse += inverse_epilogue_u8<R>(w, h == 0 ? xa : xb, store ? out0 + h : nullptr, rp,
+          sse += inverse_epilogue_u8_any<R>(w, h == 0 ? xa : xb, store ? out0 + h : nullptr, rp,
                                         store, true, 8, 8);
         }
         acc += sse;
