@@ -386,6 +386,21 @@ __device__ __forceinline__ uint2 round_pack_row_u8(const uint32_t n2[8]) {
   return make_uint2(__byte_perm(c01, c23, 0x6420u), __byte_perm(c45, c67, 0x6420u));
 }
 
+// Where the codec reads a block's samples (row k as 8 bytes): row words held
+// in registers, or re-read from a shared-memory ring slot (row stride 512 B),
+// which keeps 16 registers per block free between the forward and the
+// epilogue.
+struct RowsInRegs {
+  const uint2* x;
+  __device__ __forceinline__ uint2 row(int k) const { return x[k]; }
+};
+struct RowsInSmem {
+  const uint8_t* p;
+  __device__ __forceinline__ uint2 row(int k) const {
+    return *reinterpret_cast<const uint2*>(p + k * 512);
+  }
+};
+
 // 1: accumulate each row's SSE terms into one running sum (a dependency
 // chain across rows); 0: form each row's terms independently.
 #ifndef TDCT_SSE_CHAIN
@@ -396,8 +411,8 @@ __device__ __forceinline__ uint2 round_pack_row_u8(const uint32_t n2[8]) {
 // biased), streamed by rows into rounding, SSE terms and the store.
 // `valid_cols` = samples of each row inside the plane (8 when full),
 // `valid_rows` = rows inside the plane.  Returns sum x^2 + x'^2 - 2 x x'.
-template <int R>
-__device__ __forceinline__ uint32_t inverse_epilogue_u8(const uint32_t w[64], const uint2 x[8],
+template <int R, typename XS>
+__device__ __forceinline__ uint32_t inverse_epilogue_u8(const uint32_t w[64], XS x,
                                                         uint2* __restrict__ out_row0,
                                                         int64_t out_pitch, bool store,
                                                         bool full, int valid_rows,
@@ -426,14 +441,15 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8(const uint32_t w[64], co
       y.x &= (uint32_t)m;
       y.y &= (uint32_t)(m >> 32);
     }
+    const uint2 xk = x.row(k);
 #if TDCT_SSE_CHAIN
     acc = __dp4a(y.x, y.x, acc);
     acc = __dp4a(y.y, y.y, acc);
-    acc -= 2u * __dp4a(x[k].x, y.x, __dp4a(x[k].y, y.y, 0u));
+    acc -= 2u * __dp4a(xk.x, y.x, __dp4a(xk.y, y.y, 0u));
 #else
     // per-row partials are independent; only the final add joins them
     const uint32_t yy = __dp4a(y.x, y.x, __dp4a(y.y, y.y, 0u));
-    const uint32_t xy = __dp4a(x[k].x, y.x, __dp4a(x[k].y, y.y, 0u));
+    const uint32_t xy = __dp4a(xk.x, y.x, __dp4a(xk.y, y.y, 0u));
     acc += yy - 2u * xy;
 #endif
     if (store && full) out_row0[(int64_t)k * (out_pitch >> 3)] = y;
@@ -462,13 +478,14 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8(const uint32_t w[64], co
 
 template <int R>
 __host__ __device__ constexpr bool inverse_rows_first() {
-  return TDCT_INV_ROWS_FIRST == 2   ? kept_rows(R) < kept_cols(R)
+  return TDCT_INV_ROWS_FIRST == 3   ? kept_rows(R) <= kept_cols(R)
+         : TDCT_INV_ROWS_FIRST == 2 ? kept_rows(R) < kept_cols(R)
          : TDCT_INV_ROWS_FIRST == 1 ? (kept_cols(R) == 8 && kept_rows(R) < 8)
                                     : false;
 }
 
-template <int R>
-__device__ __forceinline__ uint32_t inverse_epilogue_u8_rows(const uint32_t w[64], const uint2 x[8],
+template <int R, typename XS>
+__device__ __forceinline__ uint32_t inverse_epilogue_u8_rows(const uint32_t w[64], XS x,
                                                              uint2* __restrict__ out_row0,
                                                              int64_t out_pitch, bool store,
                                                              bool full, int valid_rows,
@@ -511,9 +528,10 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8_rows(const uint32_t w[64
       y.x &= (uint32_t)m;
       y.y &= (uint32_t)(m >> 32);
     }
+    const uint2 xk = x.row(k);
     acc = __dp4a(y.x, y.x, acc);
     acc = __dp4a(y.y, y.y, acc);
-    acc -= 2u * __dp4a(x[k].x, y.x, __dp4a(x[k].y, y.y, 0u));
+    acc -= 2u * __dp4a(xk.x, y.x, __dp4a(xk.y, y.y, 0u));
     if (store && full) out_row0[(int64_t)k * (out_pitch >> 3)] = y;
     if (store && !full && k < valid_rows) {
       uint8_t* row = reinterpret_cast<uint8_t*>(out_row0) + (int64_t)k * out_pitch;
@@ -526,17 +544,18 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8_rows(const uint32_t w[64
 }
 
 // Inverse pass order for class R (inverse_rows_first).
-template <int R>
-__device__ __forceinline__ uint32_t inverse_epilogue_u8_any(const uint32_t w[64], const uint2 x[8],
+template <int R, typename XS>
+__device__ __forceinline__ uint32_t inverse_epilogue_u8_any(const uint32_t w[64], XS x,
                                                             uint2* __restrict__ out_row0,
                                                             int64_t out_pitch, bool store,
                                                             bool full, int valid_rows,
                                                             int valid_cols) {
   if constexpr (inverse_rows_first<R>())
-    return inverse_epilogue_u8_rows<R>(w, x, out_row0, out_pitch, store, full, valid_rows,
+    return inverse_epilogue_u8_rows<R, XS>(w, x, out_row0, out_pitch, store, full, valid_rows,
                                        valid_cols);
   else
-    return inverse_epilogue_u8<R>(w, x, out_row0, out_pitch, store, full, valid_rows, valid_cols);
+    return inverse_epilogue_u8<R, XS>(w, x, out_row0, out_pitch, store, full, valid_rows,
+                                      valid_cols);
 }
 
 // Forward pass order when the kept set is as wide as tall: 1 rows first,
@@ -549,10 +568,9 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8_any(const uint32_t w[64]
 // plane) through the packed forward and the per-block inverse.
 // FULL: the caller guarantees both blocks exist, lie inside the plane and
 // that recon (if any) has 8-byte aligned rows (the bulk-copy planes).
-template <int R, bool FULL = false>
-__device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, int bx0,
-                                                  const uint2 xa[8], const uint2 xb[8],
-                                                  const CodecParams& cp) {
+template <int R, bool FULL = false, typename XS = RowsInRegs>
+__device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, int bx0, XS xa,
+                                                  XS xb, const CodecParams& cp) {
   const bool has0 = FULL || bx0 < P.nbx, has1 = FULL || bx0 + 1 < P.nbx;
   if (!has0) return 0u;
   const int valid_rows = FULL ? 8 : min(8, P.H - by * 8);
@@ -562,10 +580,11 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
   uint32_t sse = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    sse = __dp4a(xa[k].x, xa[k].x, sse);
-    sse = __dp4a(xa[k].y, xa[k].y, sse);
-    sse = __dp4a(xb[k].x, xb[k].x, sse);
-    sse = __dp4a(xb[k].y, xb[k].y, sse);
+    const uint2 a = xa.row(k), b = xb.row(k);
+    sse = __dp4a(a.x, a.x, sse);
+    sse = __dp4a(a.y, a.y, sse);
+    sse = __dp4a(b.x, b.x, sse);
+    sse = __dp4a(b.y, b.y, sse);
   }
   // packed forward.  The first pass forms, for each of the 8 rows (or
   // columns), only the outputs inside the kept columns (rows); the second
@@ -575,7 +594,7 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
   {
     uint32_t pk[64];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) pair_row(xa[k], xb[k], pk + 8 * k);
+    for (int k = 0; k < 8; ++k) pair_row(xa.row(k), xb.row(k), pk + 8 * k);
     uint32_t t[64];
     if constexpr (TDCT_FWD_ROWS_FIRST_ON_TIE ? kept_cols(R) <= kept_rows(R) : kept_cols(R) < kept_rows(R)) {
 #pragma unroll
@@ -629,10 +648,10 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
     uint2* o = store ? (b == 0 ? out0 : out0 + 1) : nullptr;
     if (!FULL && store && !fast_store) {
       // unaligned recon or edge block: byte stores of valid samples
-      sse += inverse_epilogue_u8_any<R>(w, b == 0 ? xa : xb, o, rp, true, false, valid_rows,
+      sse += inverse_epilogue_u8_any<R, XS>(w, b == 0 ? xa : xb, o, rp, true, false, valid_rows,
                                         b == 0 ? vc0 : vc1);
     } else {
-      sse += inverse_epilogue_u8_any<R>(w, b == 0 ? xa : xb, o, rp, store, full, valid_rows,
+      sse += inverse_epilogue_u8_any<R, XS>(w, b == 0 ? xa : xb, o, rp, store, full, valid_rows,
                                         b == 0 ? vc0 : vc1);
     }
   }
@@ -654,7 +673,7 @@ __device__ __forceinline__ uint32_t codec_lane_u8(const PlaneDesc& P, int by, in
 #pragma unroll
     for (int k = 0; k < 8; ++k) rb.w[k] = make_uint2(0u, 0u);
   }
-  return codec_pair_u8<R>(P, by, bx0, ra.w, rb.w, cp);
+  return codec_pair_u8<R>(P, by, bx0, RowsInRegs{ra.w}, RowsInRegs{rb.w}, cp);
 }
 
 // Persistent fused codec: every warp takes a contiguous range of units.
@@ -807,30 +826,36 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t U = tab.total_units;
   const int64_t u_begin = (U * warp) / nwarps;
-  const int64_t u_end = (U * (warp + 1)) / nwarps;
+  // The warp's units are counted from u_begin in 32 bits (fewer live
+  // registers across the loop): a unit holds at least 8 rows x 16 bytes of
+  // a ring plane, so even a full device gives under 2^31 units per warp.
+  const int n_units = (int)((U * (warp + 1)) / nwarps - u_begin);
+  const bool hook = cp.test_hook == 1 && warp == 0;
 
   // producer cursor: the plane of the next unit to prefetch and the unit's
   // (block-row, chunk) within it, advanced incrementally (a division only
   // when the cursor enters a plane)
-  int64_t pp_end = -1, pp_pitch = 0;
+  int64_t pp_pitch = 0;
   const uint8_t* pp_img = nullptr;
-  int pp_W = 0, pp_chunks = 1, pp_by = 0, pp_chunk = 0, pp_s = 0;
+  int pp_end = -1, pp_W = 0, pp_chunks = 1, pp_by = 0, pp_chunk = 0, pp_s = 0;
   uint32_t issued = 0;  // bit s: slot s holds a copy in flight
   uint32_t phase = 0;   // bit s: parity of slot s's next completion
-  int64_t u_pf = u_begin;
+  int pf = 0;           // next unit to prefetch (from u_begin)
 
   auto issue_next = [&]() {
-    const int64_t u = u_pf++;
+    const int i = pf++;
     const int s = pp_s;
     pp_s = pp_s + 1 == STAGES ? 0 : pp_s + 1;
-    if (u >= pp_end) {
+    if (i >= pp_end) {
+      const int64_t u = u_begin + i;
       const int q = find_plane(tab, u);
       const PlaneDesc& Q = tab.d ? tab.d[q] : tab.one;
       pp_img = Q.img;
       pp_pitch = Q.pitch;
       pp_W = Q.W;
       pp_chunks = Q.chunks;
-      pp_end = (q + 1 < tab.n) ? tab.d[q + 1].unit_begin : U;
+      const int64_t e = ((q + 1 < tab.n) ? tab.d[q + 1].unit_begin : U) - u_begin;
+      pp_end = (int)(e < n_units ? e : n_units);
       const int64_t local = u - Q.unit_begin;
       pp_by = (int)(local / pp_chunks);
       pp_chunk = (int)(local - (int64_t)pp_by * pp_chunks);
@@ -846,7 +871,7 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (lane == 0) mbar_arrive_expect_tx(bar, 8u * row_bytes);
     __syncwarp();
-    const bool skip = cp.test_hook == 1 && warp == 0 && u == u_begin;
+    const bool skip = hook && i == 0;
     if (lane < 8 && !skip) {
       const uint8_t* src = pp_img + (int64_t)(by * 8 + lane) * pp_pitch + (int64_t)chunk * 512;
       bulk_copy_g2s(smem_addr(ring + s * kUnitBytes + lane * 512), src, row_bytes, bar);
@@ -870,23 +895,25 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
     return false;
   };
 
-  for (int k = 0; k < STAGES && u_pf < u_end; ++k) issue_next();
+  for (int k = 0; k < STAGES && pf < n_units; ++k) issue_next();
 
   int p = -1;
-  int64_t p_end = -1;
+  int p_end = -1;
   PlaneDesc P;
   int by = 0, chunk = 0, s = 0;  // consumer cursor, advanced like the producer's
   unsigned long long acc = 0;
-  for (int64_t u = u_begin; u < u_end; ++u) {
-    if (u >= p_end) {
+  for (int i = 0; i < n_units; ++i) {
+    if (i >= p_end) {
       if (p >= 0) {
         acc = warp_sum_u64(acc);
         if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
         acc = 0;
       }
+      const int64_t u = u_begin + i;
       p = find_plane(tab, u);
       P = tab.d ? tab.d[p] : tab.one;
-      p_end = (p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U;
+      const int64_t e = ((p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U) - u_begin;
+      p_end = (int)(e < n_units ? e : n_units);
       const int64_t local = u - P.unit_begin;
       by = (int)(local / P.chunks);
       chunk = (int)(local - (int64_t)by * P.chunks);
@@ -899,17 +926,13 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
     }
     s = s + 1 == STAGES ? 0 : s + 1;
     if (!wait_slot(cur_s)) return;
-    uint2 xa[8], xb[8];
+    // the lane's two blocks stay in the slot: the forward reads them, the
+    // epilogue reads them again for the SSE; the slot is refilled after
     const uint8_t* slot = ring + cur_s * kUnitBytes + lane * 16;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint4 v = *reinterpret_cast<const uint4*>(slot + k * 512);
-      xa[k] = make_uint2(v.x, v.y);
-      xb[k] = make_uint2(v.z, v.w);
-    }
+    if (bx0 < P.nbx)
+      acc += codec_pair_u8<R, true>(P, cur_by, bx0, RowsInSmem{slot}, RowsInSmem{slot + 8}, cp);
     __syncwarp();
-    if (u_pf < u_end) issue_next();  // refill the slot just read
-    if (bx0 < P.nbx) acc += codec_pair_u8<R, true>(P, cur_by, bx0, xa, xb, cp);
+    if (pf < n_units) issue_next();  // refill the slot just used
   }
   if (p >= 0) {
     acc = warp_sum_u64(acc);
@@ -917,9 +940,11 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
   }
 }
 
-// Slots per warp of the bulk-copy ring (3 CTAs x 4 warps x 3 x 4 KB = 144 KB per SM).
+// Slots per warp of the bulk-copy ring (3 CTAs x 4 warps x 4 x 4 KB = 192 KB
+// per SM); a slot is refilled after its unit is done, so 3 units stay in
+// flight while one is computed.
 #ifndef TDCT_U8_STAGES
-#define TDCT_U8_STAGES 3
+#define TDCT_U8_STAGES 4
 #endif
 
 inline int device_sms() {

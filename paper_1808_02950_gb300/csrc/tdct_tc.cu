@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, false>())
             }
           }
         w[0] += kL2;
-        sse += inverse_epilogue_u8_any<R>(w, b == 0 ? xa : xb, store ? out0 + b : nullptr, rp, store,
+        sse += inverse_epilogue_u8_any<R>(w, RowsInRegs{b == 0 ? xa : xb}, store ? out0 + b : nullptr, rp, store,
                                       true, 8, 8);
       }
       acc += sse;
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, true>())
               }
             }
           w[0] += kL2;
-          sse += inverse_epilogue_u8_any<R>(w, h == 0 ? xa : xb, store ? out0 + h : nullptr, rp,
+          sse += inverse_epilogue_u8_any<R>(w, RowsInRegs{h == 0 ? xa : xb}, store ? out0 + h : nullptr, rp,
                                         store, true, 8, 8);
         }
         acc += sse;
