@@ -185,6 +185,34 @@ int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, cons
                                      tdct_stream_t stream);
 
 /*
+ * tdct_codec_error_batched_host -- tdct_codec_error_batched on planes that
+ * live in HOST memory, with the results returned to host memory (§6.1 per
+ * plane; same kernels, same bit-exact results).  The copies to the device
+ * are pipelined with the codec: consecutive planes are grouped into chunks
+ * of about `chunk_bytes` (0 = 64 MiB; a larger plane forms its own chunk),
+ * staged in two device buffers, and chunk c + 1 is copied while chunk c is
+ * coded (and, when reconstructions are requested, chunk c - 1's are copied
+ * back).  The transfers use two library-owned non-blocking streams per
+ * device (created on first use, kept until exit); device memory comes from
+ * the stream-ordered pool and is released on `stream`.
+ *   planes    host array of nplanes descriptors whose img / recon are HOST
+ *             pointers (recon may be NULL: no reconstruction is copied back).
+ *             Page-locked memory lets the copies run at the link's rate and
+ *             asynchronously; pageable memory works through the driver's
+ *             staging.
+ *   h_sse     host output, uint64 [nplanes]
+ *   h_psnr    host output or NULL, double [nplanes]
+ * Asynchronous on `stream`: outputs and reconstructions are complete when
+ * `stream` has completed the call's work (with pageable h_sse / h_psnr the
+ * call returns only after they are written).  The host buffers must stay
+ * valid until then.  Errors: as tdct_codec_error_batched (the engine is the
+ * CUDA-core one).
+ */
+int tdct_codec_error_batched_host(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                                  const int32_t n[8], uint64_t* h_sse, double* h_psnr,
+                                  size_t chunk_bytes, tdct_stream_t stream);
+
+/*
  * Batch plans: the same work as tdct_codec_error_batched, prepared once
  * (validation, block-offset table in device memory, launch configuration)
  * and replayed as one CUDA graph per launch.  The plan owns its device

@@ -33,7 +33,7 @@ N1 = (8, 18, 20, 18, 8, 18, 20, 18)
 
 EXPORTS = (
     "tdct_forward", "tdct_zonal_inverse", "tdct_codec_error", "tdct_codec_error_batched",
-    "tdct_codec_error_batched_noalloc",
+    "tdct_codec_error_batched_noalloc", "tdct_codec_error_batched_host",
     "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_config",
     "tdct_plan_destroy",
     "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_codec_error.argtypes = [vp, i64, i32, i32, i32, vp, vp, i32, vp, i64, vp, vp, vp]
     L.tdct_codec_error_batched.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
     L.tdct_codec_error_batched_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.tdct_codec_error_batched_host.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.tdct_plan_create.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_void_p)]
     L.tdct_plan_launch.argtypes = [vp, vp, vp, vp]
     L.tdct_plan_kernel_count.argtypes = [vp]
@@ -206,6 +207,18 @@ def tdct_codec_error_batched_noalloc(planes, sse, psnr=None, T=None, n=None, str
     tb, nb = _T_n(T, n)
     _check(load().tdct_codec_error_batched_noalloc(ctypes.addressof(planes), len(planes), tb, nb,
                                                    _ptr(sse), _ptr(psnr), _stream(stream)))
+
+
+def tdct_codec_error_batched_host(planes, sse, psnr=None, T=None, n=None, chunk_bytes=0,
+                                  stream=None) -> None:
+    """The batched codec on planes in host memory (``make_planes`` over CPU
+    tensors; pinned tensors let the copies overlap the codec); SSE / PSNR
+    land in the CPU tensors ``sse`` / ``psnr`` once ``stream`` reaches the
+    end of the call's work."""
+    tb, nb = _T_n(T, n)
+    _check(load().tdct_codec_error_batched_host(ctypes.addressof(planes), len(planes), tb, nb,
+                                                _ptr(sse), _ptr(psnr), int(chunk_bytes),
+                                                _stream(stream)))
 
 
 class TdctPlan:

@@ -821,6 +821,106 @@ int noalloc_scratch(void** out) {
   *out = g_noalloc_addr[dev];
   return TDCT_OK;
 }
+
+// Library-owned transfer streams of tdct_codec_error_batched_host, one pair
+// per device, created on first use.
+struct HostStreams {
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+};
+std::mutex g_host_mu;
+HostStreams g_host_streams[256];
+
+int host_streams(HostStreams* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(TDCT_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_host_mu);
+  HostStreams& hs = g_host_streams[dev];
+  if (!hs.h2d && (e = cudaStreamCreateWithFlags(&hs.h2d, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "transfer stream");
+  if (!hs.d2h && (e = cudaStreamCreateWithFlags(&hs.d2h, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "transfer stream");
+  *out = hs;
+  return TDCT_OK;
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Copies between host planes and their staged images: planes whose rows are
+// contiguous and that follow each other without a gap both on the host and
+// in the staging buffer are merged into one linear copy (one DMA request
+// instead of one per plane); other planes take a 2-D copy each.
+// `host_of(i)` / `host_pitch(i)` give plane i's host side (input or
+// reconstruction).
+template <typename HostOf, typename PitchOf>
+cudaError_t copy_planes(const tdct_plane* planes, int first, int count, uint8_t* staged,
+                        const std::vector<size_t>& off, const std::vector<int64_t>& dpitch,
+                        HostOf host_of, PitchOf host_pitch, bool to_device, cudaStream_t st,
+                        int* failed_plane) {
+  int k = 0;
+  while (k < count) {
+    const int i = first + k;
+    const tdct_plane& p = planes[i];
+    const size_t row = (size_t)p.W * (p.dtype == TDCT_I16 ? 2 : 1);
+    uint8_t* h = static_cast<uint8_t*>(const_cast<void*>(host_of(i)));
+    if (!h) {
+      ++k;
+      continue;
+    }
+    const bool linear = (size_t)host_pitch(i) == row && (size_t)dpitch[i] == row;
+    if (!linear) {
+      const cudaError_t e =
+          to_device ? cudaMemcpy2DAsync(staged + off[i], (size_t)dpitch[i], h, (size_t)host_pitch(i),
+                                        row, (size_t)p.H, cudaMemcpyHostToDevice, st)
+                    : cudaMemcpy2DAsync(h, (size_t)host_pitch(i), staged + off[i], (size_t)dpitch[i],
+                                        row, (size_t)p.H, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) {
+        *failed_plane = i;
+        return e;
+      }
+      ++k;
+      continue;
+    }
+    size_t bytes = row * (size_t)p.H;
+    int m = k + 1;
+    while (m < count) {
+      const int j = first + m;
+      const tdct_plane& q = planes[j];
+      const size_t qrow = (size_t)q.W * (q.dtype == TDCT_I16 ? 2 : 1);
+      const uint8_t* hq = static_cast<const uint8_t*>(host_of(j));
+      if (!hq || (size_t)host_pitch(j) != qrow || (size_t)dpitch[j] != qrow || hq != h + bytes ||
+          off[j] != off[i] + bytes)
+        break;
+      bytes += qrow * (size_t)q.H;
+      ++m;
+    }
+    auto linear_copy = [&](int j, size_t n) {
+      uint8_t* hj = static_cast<uint8_t*>(const_cast<void*>(host_of(j)));
+      return to_device ? cudaMemcpyAsync(staged + off[j], hj, n, cudaMemcpyHostToDevice, st)
+                       : cudaMemcpyAsync(hj, staged + off[j], n, cudaMemcpyDeviceToHost, st);
+    };
+    cudaError_t e = linear_copy(i, bytes);
+    if (e == cudaErrorInvalidValue && m > k + 1) {
+      // Adjacent planes from different host allocations: the driver rejects
+      // a range that crosses page-locked allocations (argument check,
+      // nothing enqueued).  Clear that error and copy the run plane by plane.
+      (void)cudaGetLastError();
+      e = cudaSuccess;
+      for (int t = k; t < m && e == cudaSuccess; ++t) {
+        const tdct_plane& q = planes[first + t];
+        e = linear_copy(first + t, (size_t)q.W * (q.dtype == TDCT_I16 ? 2 : 1) * (size_t)q.H);
+        if (e != cudaSuccess) *failed_plane = first + t;
+      }
+      if (e != cudaSuccess) return e;
+    } else if (e != cudaSuccess) {
+      *failed_plane = i;
+      return e;
+    }
+    k = m;
+  }
+  return cudaSuccess;
+}
 }  // namespace
 
 extern "C" {
@@ -856,6 +956,181 @@ int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, cons
     e = enqueue_batch(tr, groups, d_descs, d_npix, nplanes,
                       reinterpret_cast<unsigned long long*>(d_sse), d_psnr, s);
   return e == cudaSuccess ? TDCT_OK : cuda_fail(e, "tdct_codec_error_batched_noalloc");
+}
+
+int tdct_codec_error_batched_host(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                                  const int32_t n[8], uint64_t* h_sse, double* h_psnr,
+                                  size_t chunk_bytes, tdct_stream_t stream) {
+  Transform tr;
+  int rc = resolve_transform(T, n, &tr);
+  if (rc) return rc;
+  if (!planes || nplanes < 1 || nplanes > (1 << 20))
+    return fail(TDCT_EINVAL, "nplanes = %d outside 1..2^20 (or planes is NULL)", nplanes);
+  if (!h_sse) return fail(TDCT_EINVAL, "h_sse is NULL");
+  if (chunk_bytes == 0) chunk_bytes = (size_t)64 << 20;
+
+  // Staged layout: each plane row-contiguous with a 16-byte multiple pitch
+  // (u8 planes with W % 16 == 0 and H % 8 == 0 then take the bulk-copy
+  // ring), 256-byte aligned, packed into chunks of consecutive planes.
+  std::vector<size_t> off(nplanes);
+  std::vector<int64_t> dpitch(nplanes);
+  std::vector<int> chunk_first;
+  size_t cur = 0, max_chunk = 0;
+  bool any_recon = false;
+  for (int i = 0; i < nplanes; ++i) {
+    const tdct_plane& p = planes[i];
+    char what[64];
+    std::snprintf(what, sizeof what, "plane %d", i);
+    if ((rc = check_plane(p.img, p.pitch, p.H, p.W, p.dtype, what))) return rc;
+    if (p.r < 1 || p.r > 64) return fail(TDCT_EINVAL, "plane %d: r = %d outside 1..64", i, p.r);
+    if (p.recon && p.recon_pitch < (int64_t)p.W * sample_bytes(p.dtype))
+      return fail(TDCT_EINVAL, "plane %d: recon pitch too small", i);
+    dpitch[i] = (int64_t)round_up((size_t)p.W * sample_bytes(p.dtype), 16);
+    const size_t bytes = round_up((size_t)dpitch[i] * p.H, 256);
+    if (i == 0 || (cur > 0 && cur + bytes > chunk_bytes)) {
+      chunk_first.push_back(i);
+      cur = 0;
+    }
+    off[i] = cur;
+    cur += bytes;
+    max_chunk = std::max(max_chunk, cur);
+    any_recon |= p.recon != nullptr;
+  }
+  const int nchunks = (int)chunk_first.size();
+  chunk_first.push_back(nplanes);
+
+  HostStreams hs;
+  if ((rc = host_streams(&hs))) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+  // One stream-ordered block: 2 input buffers, 2 reconstruction buffers (if
+  // any), the descriptor table and sample counts, SSE and PSNR.
+  const size_t bytes_desc = round_up(sizeof(PlaneDesc) * nplanes, 256);
+  const size_t bytes_npix = round_up(sizeof(int64_t) * nplanes, 256);
+  const size_t bytes_res = round_up(sizeof(uint64_t) * nplanes, 256);
+  const size_t nbuf = any_recon ? 4 : 2;
+  const size_t total = nbuf * max_chunk + bytes_desc + bytes_npix + 2 * bytes_res;
+  void* block = nullptr;
+  cudaError_t e = cudaMallocAsync(&block, total, s);
+  if (e != cudaSuccess) return fail(TDCT_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  uint8_t* base = static_cast<uint8_t*>(block);
+  uint8_t* in_buf[2] = {base, base + max_chunk};
+  uint8_t* out_buf[2] = {any_recon ? base + 2 * max_chunk : nullptr,
+                         any_recon ? base + 3 * max_chunk : nullptr};
+  PlaneDesc* d_descs = reinterpret_cast<PlaneDesc*>(base + nbuf * max_chunk);
+  int64_t* d_npix = reinterpret_cast<int64_t*>(base + nbuf * max_chunk + bytes_desc);
+  unsigned long long* d_sse =
+      reinterpret_cast<unsigned long long*>(base + nbuf * max_chunk + bytes_desc + bytes_npix);
+  double* d_psnr = reinterpret_cast<double*>(base + nbuf * max_chunk + bytes_desc + bytes_npix +
+                                             bytes_res);
+
+  // Per-chunk block-offset tables over the staged planes (slots relative to
+  // the chunk), all uploaded at once.
+  std::vector<PlaneDesc> descs(nplanes);
+  std::vector<int64_t> npix(nplanes);
+  std::vector<std::vector<Group>> groups(nchunks);
+  for (int c = 0; c < nchunks && rc == TDCT_OK; ++c) {
+    const int first = chunk_first[c], count = chunk_first[c + 1] - first;
+    std::vector<tdct_plane> staged(count);
+    for (int k = 0; k < count; ++k) {
+      const tdct_plane& p = planes[first + k];
+      staged[k] = p;
+      staged[k].img = in_buf[c & 1] + off[first + k];
+      staged[k].pitch = dpitch[first + k];
+      staged[k].recon = p.recon ? out_buf[c & 1] + off[first + k] : nullptr;
+      staged[k].recon_pitch = p.recon ? dpitch[first + k] : 0;
+    }
+    std::vector<PlaneDesc> dc;
+    std::vector<int64_t> nc;
+    rc = build_batch(staged.data(), count, dc, groups[c], nc);
+    if (rc == TDCT_OK) {
+      std::copy(dc.begin(), dc.end(), descs.begin() + first);
+      std::copy(nc.begin(), nc.end(), npix.begin() + first);
+    }
+  }
+  cudaEvent_t ev_start = nullptr, ev_end_d2h = nullptr, ev_h2d[2] = {}, ev_comp[2] = {},
+              ev_d2h[2] = {};
+  auto make_events = [&]() -> cudaError_t {
+    cudaError_t x = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+    if (x == cudaSuccess) x = cudaEventCreateWithFlags(&ev_end_d2h, cudaEventDisableTiming);
+    for (int b = 0; b < 2 && x == cudaSuccess; ++b) {
+      x = cudaEventCreateWithFlags(&ev_h2d[b], cudaEventDisableTiming);
+      if (x == cudaSuccess) x = cudaEventCreateWithFlags(&ev_comp[b], cudaEventDisableTiming);
+      if (x == cudaSuccess) x = cudaEventCreateWithFlags(&ev_d2h[b], cudaEventDisableTiming);
+    }
+    return x;
+  };
+  int bad_plane = -1;
+  const char* what = "setup";
+  if (rc == TDCT_OK) {
+    e = make_events();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_descs, descs.data(), sizeof(PlaneDesc) * nplanes,
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_npix, npix.data(), sizeof(int64_t) * nplanes, cudaMemcpyHostToDevice,
+                          s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hs.h2d, ev_start, 0);
+    if (e == cudaSuccess && any_recon) e = cudaStreamWaitEvent(hs.d2h, ev_start, 0);
+    for (int c = 0; c < nchunks && e == cudaSuccess; ++c) {
+      const int b = c & 1, first = chunk_first[c], count = chunk_first[c + 1] - first;
+      // input buffer b is free once chunk c - 2 has been coded
+      if (c >= 2) e = cudaStreamWaitEvent(hs.h2d, ev_comp[b], 0);
+      if (e == cudaSuccess)
+        e = copy_planes(
+            planes, first, count, in_buf[b], off, dpitch,
+            [&](int i) { return planes[i].img; }, [&](int i) { return planes[i].pitch; }, true,
+            hs.h2d, &bad_plane);
+      if (e != cudaSuccess) what = "copy to the device";
+      if (e == cudaSuccess) e = cudaEventRecord(ev_h2d[b], hs.h2d);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_h2d[b], 0);
+      // reconstruction buffer b is free once chunk c - 2's copies back are done
+      if (e == cudaSuccess && any_recon && c >= 2) e = cudaStreamWaitEvent(s, ev_d2h[b], 0);
+      if (e == cudaSuccess) {
+        e = enqueue_batch(tr, groups[c], d_descs + first, d_npix + first, count, d_sse + first,
+                          h_psnr ? d_psnr + first : nullptr, s);
+        if (e != cudaSuccess) what = "codec launch";
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev_comp[b], s);
+      if (e == cudaSuccess && any_recon) {
+        e = cudaStreamWaitEvent(hs.d2h, ev_comp[b], 0);
+        if (e == cudaSuccess)
+          e = copy_planes(
+              planes, first, count, out_buf[b], off, dpitch,
+              [&](int i) { return static_cast<const void*>(planes[i].recon); },
+              [&](int i) { return planes[i].recon_pitch; }, false, hs.d2h, &bad_plane);
+        if (e != cudaSuccess) what = "copy of the reconstruction";
+        if (e == cudaSuccess) e = cudaEventRecord(ev_d2h[b], hs.d2h);
+      }
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_sse, d_sse, sizeof(uint64_t) * nplanes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_psnr)
+      e = cudaMemcpyAsync(h_psnr, d_psnr, sizeof(double) * nplanes, cudaMemcpyDeviceToHost, s);
+  }
+  // `stream` waits for everything the transfer streams hold (also after a
+  // failed enqueue), so the block is released in stream order after its
+  // last use.
+  cudaError_t ew = cudaSuccess;
+  if (ev_start) {
+    ew = cudaEventRecord(ev_h2d[0], hs.h2d);
+    if (ew == cudaSuccess) ew = cudaStreamWaitEvent(s, ev_h2d[0], 0);
+    if (ew == cudaSuccess && any_recon) ew = cudaEventRecord(ev_end_d2h, hs.d2h);
+    if (ew == cudaSuccess && any_recon) ew = cudaStreamWaitEvent(s, ev_end_d2h, 0);
+  }
+  const cudaError_t ef = cudaFreeAsync(block, s);
+  for (cudaEvent_t ev : {ev_start, ev_end_d2h, ev_h2d[0], ev_h2d[1], ev_comp[0], ev_comp[1],
+                         ev_d2h[0], ev_d2h[1]})
+    if (ev) cudaEventDestroy(ev);
+  if (rc) return rc;
+  if (e != cudaSuccess)
+    return fail(TDCT_ECUDA, "tdct_codec_error_batched_host: %s%s%s: %s", what,
+                bad_plane >= 0 ? " of plane " : "",
+                bad_plane >= 0 ? std::to_string(bad_plane).c_str() : "", cudaGetErrorString(e));
+  if (ew != cudaSuccess) return cuda_fail(ew, "tdct_codec_error_batched_host: stream join");
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  return TDCT_OK;
 }
 
 int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype, int r,

@@ -183,3 +183,20 @@ def test_named_transforms_agree_with_the_oracle_copies():
         assert np.array_equal(np.array(T), want[name]), name
         assert tr.row_norms(T) == tuple(int(v) for v in np.einsum("ij,ij->i", want[name], want[name]))
     assert tr.T1 == tuple(tuple(r) for r in P.T1)
+
+
+def test_host_buffer_batch_rejects_before_any_cuda_call():
+    L = P.load()
+    tb, nb = _lib._T_n()
+    good = (FAKE, 64, 16, 64, 10, 0, 0, 0)
+    planes = P.make_planes_raw([good, (FAKE, 64, 16, 64, 70, 0, 0, 0)])
+    rc = L.tdct_codec_error_batched_host(ctypes.addressof(planes), 2, tb, nb, FAKE, None, 0, None)
+    assert rc == _lib.TDCT_EINVAL and "plane 1" in L.tdct_last_error().decode()
+    planes = P.make_planes_raw([good])
+    assert L.tdct_codec_error_batched_host(ctypes.addressof(planes), 1, tb, nb, None, None, 0,
+                                           None) == _lib.TDCT_EINVAL
+    assert L.tdct_codec_error_batched_host(ctypes.addressof(planes), 0, tb, nb, FAKE, None, 0,
+                                           None) == _lib.TDCT_EINVAL
+    planes = P.make_planes_raw([(None, 64, 16, 64, 10, 0, 0, 0)])
+    assert L.tdct_codec_error_batched_host(ctypes.addressof(planes), 1, tb, nb, FAKE, None, 0,
+                                           None) == _lib.TDCT_EINVAL
