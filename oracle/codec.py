@@ -74,6 +74,10 @@ def lib() -> ctypes.CDLL:
         L.orc_psnr.argtypes = [ctypes.c_int64, ctypes.c_int64]
         L.orc_psnr.restype = ctypes.c_double
         L.orc_dct_matrix.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        L.orc_ssim_plane.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double)]
+        L.orc_ssim_plane.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -168,6 +172,20 @@ def dct_codec_plane(img: np.ndarray, r: int, want_recon: bool = True, want_coef:
     if rc != 0:
         raise ValueError(f"oracle dct_codec_plane failed with code {rc}")
     return sse.value, recon, coef
+
+
+def ssim_plane(x: np.ndarray, y: np.ndarray) -> float:
+    """MSSIM of two u8 planes (Wang et al. 2004 window and constants, valid
+    window positions only); raises ValueError below 11 x 11."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    y = np.ascontiguousarray(y, dtype=np.uint8)
+    assert x.shape == y.shape and x.ndim == 2
+    out = ctypes.c_double(0.0)
+    rc = lib().orc_ssim_plane(x.ctypes.data, x.strides[0], y.ctypes.data, y.strides[0],
+                              x.shape[0], x.shape[1], ctypes.byref(out))
+    if rc != 0:
+        raise ValueError("SSIM needs planes of at least 11 x 11 samples")
+    return out.value
 
 
 def psnr(sse: int, npix: int) -> float:

@@ -339,3 +339,55 @@ double orc_psnr(int64_t sse, int64_t npix) {
   double mse = (double)sse / (double)npix;
   return 10.0 * log10(255.0 * 255.0 / mse);
 }
+
+/*
+ * Mean structural similarity (MSSIM) of two u8 planes.  §6.1 evaluates the
+ * reconstructions with SSIM as defined by Wang, Bovik, Sheikh and Simoncelli
+ * (2004); the parameters are that paper's: an 11x11 circular-symmetric
+ * Gaussian weighting window w (standard deviation 1.5 samples, normalised to
+ * unit sum), K1 = 0.01, K2 = 0.03, dynamic range L = 255.  At every position
+ * where the window lies entirely inside the plane (no padding):
+ *   mx = sum w x,  sx^2 = sum w (x - mx)^2,  sxy = sum w (x - mx)(y - my),
+ *   SSIM = ((2 mx my + C1)(2 sxy + C2)) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2))
+ * with C1 = (K1 L)^2, C2 = (K2 L)^2; MSSIM = the mean of SSIM over those
+ * positions.  Everything by the definition (two passes over each window),
+ * in double.  Returns ORC_EINVAL when the plane is smaller than the window.
+ */
+int orc_ssim_plane(const uint8_t* x, int64_t xpitch, const uint8_t* y, int64_t ypitch, int H,
+                   int W, double* mssim) {
+  enum { WIN = 11, HALF = 5 };
+  if (H < WIN || W < WIN) return ORC_EINVAL;
+  double w[WIN][WIN], wsum = 0.0;
+  for (int i = 0; i < WIN; ++i)
+    for (int j = 0; j < WIN; ++j) {
+      const double di = i - HALF, dj = j - HALF;
+      w[i][j] = exp(-(di * di + dj * dj) / (2.0 * 1.5 * 1.5));
+      wsum += w[i][j];
+    }
+  for (int i = 0; i < WIN; ++i)
+    for (int j = 0; j < WIN; ++j) w[i][j] /= wsum;
+  const double C1 = (0.01 * 255.0) * (0.01 * 255.0), C2 = (0.03 * 255.0) * (0.03 * 255.0);
+  double total = 0.0;
+  for (int r0 = 0; r0 + WIN <= H; ++r0)
+    for (int c0 = 0; c0 + WIN <= W; ++c0) {
+      double mx = 0.0, my = 0.0;
+      for (int i = 0; i < WIN; ++i)
+        for (int j = 0; j < WIN; ++j) {
+          mx += w[i][j] * x[(int64_t)(r0 + i) * xpitch + c0 + j];
+          my += w[i][j] * y[(int64_t)(r0 + i) * ypitch + c0 + j];
+        }
+      double sxx = 0.0, syy = 0.0, sxy = 0.0;
+      for (int i = 0; i < WIN; ++i)
+        for (int j = 0; j < WIN; ++j) {
+          const double dx = x[(int64_t)(r0 + i) * xpitch + c0 + j] - mx;
+          const double dy = y[(int64_t)(r0 + i) * ypitch + c0 + j] - my;
+          sxx += w[i][j] * dx * dx;
+          syy += w[i][j] * dy * dy;
+          sxy += w[i][j] * dx * dy;
+        }
+      total += ((2.0 * mx * my + C1) * (2.0 * sxy + C2)) /
+               ((mx * mx + my * my + C1) * (sxx + syy + C2));
+    }
+  *mssim = total / ((double)(H - WIN + 1) * (double)(W - WIN + 1));
+  return ORC_OK;
+}

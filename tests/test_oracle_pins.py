@@ -365,3 +365,76 @@ def test_dct_codec_fp64_properties():
     # r = 1 reconstruction is the rounded block mean
     _, rec1, _ = oc.dct_codec_plane(img, 1)
     assert np.all(rec1[:8, :8] == np.floor(X.mean() + 0.5))
+
+
+# ---- SSIM (§6.1, the index of Wang et al. 2004) ---------------------------------
+
+_C1, _C2 = (0.01 * 255) ** 2, (0.03 * 255) ** 2
+
+
+def _library_window():
+    from scipy.signal import windows
+
+    g = windows.gaussian(11, std=1.5)
+    w = np.outer(g, g)
+    return w / w.sum()
+
+
+def _library_mssim(x, y):
+    """MSSIM from scipy's Gaussian window and valid-mode correlations, with
+    the moments written as E[x^2] - E[x]^2 (a different route to the same
+    statistics)."""
+    from scipy.signal import correlate2d
+
+    w = _library_window()
+    x = x.astype(np.float64)
+    y = y.astype(np.float64)
+    mx, my = correlate2d(x, w, "valid"), correlate2d(y, w, "valid")
+    sxx = correlate2d(x * x, w, "valid") - mx * mx
+    syy = correlate2d(y * y, w, "valid") - my * my
+    sxy = correlate2d(x * y, w, "valid") - mx * my
+    m = ((2 * mx * my + _C1) * (2 * sxy + _C2)) / ((mx * mx + my * my + _C1) * (sxx + syy + _C2))
+    return m.mean()
+
+
+@pytest.mark.parametrize("H,W", [(11, 11), (20, 33), (64, 64), (37, 12)])
+def test_ssim_matches_library_statistics(H, W):
+    rng = np.random.default_rng(H * 100 + W)
+    x = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    y = np.clip(x.astype(int) + rng.integers(-40, 41, (H, W)), 0, 255).astype(np.uint8)
+    assert oc.ssim_plane(x, y) == pytest.approx(_library_mssim(x, y), abs=1e-12)
+    assert oc.ssim_plane(x, y) == pytest.approx(oc.ssim_plane(y, x), abs=1e-15)
+
+
+def test_ssim_identical_planes_is_one():
+    rng = np.random.default_rng(1)
+    x = rng.integers(0, 256, (30, 41)).astype(np.uint8)
+    assert oc.ssim_plane(x, x) == pytest.approx(1.0, abs=1e-14)
+
+
+@pytest.mark.parametrize("a,b", [(0, 0), (0, 255), (100, 120), (255, 7)])
+def test_ssim_constant_planes_closed_form(a, b):
+    # zero variances: SSIM = (2ab + C1) / (a^2 + b^2 + C1) at every position
+    x = np.full((16, 19), a, np.uint8)
+    y = np.full((16, 19), b, np.uint8)
+    want = (2 * a * b + _C1) / (a * a + b * b + _C1)
+    assert oc.ssim_plane(x, y) == pytest.approx(want, rel=1e-13)
+
+
+def test_ssim_luminance_shift_leaves_only_the_luminance_term():
+    # y = x + c (no clipping): sy = sx and sxy = sx^2, so the contrast-structure
+    # factor is 1 and SSIM = (2 mx (mx + c) + C1) / (mx^2 + (mx + c)^2 + C1)
+    from scipy.signal import correlate2d
+
+    rng = np.random.default_rng(2)
+    x = rng.integers(0, 200, (25, 28)).astype(np.uint8)
+    c = 37
+    y = (x.astype(int) + c).astype(np.uint8)
+    mx = correlate2d(x.astype(np.float64), _library_window(), "valid")
+    want = ((2 * mx * (mx + c) + _C1) / (mx * mx + (mx + c) ** 2 + _C1)).mean()
+    assert oc.ssim_plane(x, y) == pytest.approx(want, abs=1e-12)
+
+
+def test_ssim_needs_a_full_window():
+    with pytest.raises(ValueError):
+        oc.ssim_plane(np.zeros((10, 40), np.uint8), np.zeros((10, 40), np.uint8))
