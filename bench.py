@@ -52,6 +52,8 @@ def parse():
                     help="the 8-point matrix (T1: fused kernels; others: generic kernels)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ssim", action="store_true",
+                    help="skip the MSSIM measurement (originals vs reconstructions)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU-oracle sample budget (seconds of host work)")
     return ap.parse_args()
@@ -363,6 +365,36 @@ def time_ours(args, dist, out):
                       "h2d_bytes_per_step": int(wl.in_bytes), "d2h_bytes_per_step": 16 * n,
                       "steps": ke, "call": "tdct_codec_error_batched_host",
                       "reconstruction_returned": False}
+    # MSSIM of every image against its reconstruction (the third figure of
+    # merit of the paper's image experiment), timed separately: FP32 work on
+    # the CUDA cores, reported against the FP32 FMA peak from unit counts and
+    # clocks (152 SMs x 128 lanes x 2 FLOP x max SM clock).
+    u8_planes = [(pl, rc) for (pl, _), rc in zip(wl.planes, wl.recons) if pl.dtype == torch.uint8]
+    if not args.no_ssim and u8_planes:
+        plan.launch(sse, psnr, stream)  # reconstructions of the timed configuration
+        mssim = torch.zeros(len(u8_planes), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            P.tdct_ssim_batched(u8_planes, mssim, stream)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        ks = 5
+        s0.record(stream)
+        for _ in range(ks):
+            P.tdct_ssim_batched(u8_planes, mssim, stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / ks
+        windows = sum((pl.shape[0] - 10) * (pl.shape[1] - 10) for pl, _ in u8_planes)
+        flops = 245.0 * windows  # 5 maps x 11 taps x 2 passes x 2 FLOP + the index
+        sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        out["ssim"] = {"value": windows / (ms / 1e3), "unit": "windows/s", "ms": ms,
+                       "blocks_per_s": wl.blocks / (ms / 1e3), "mean_mssim": mssim.mean().item(),
+                       "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12,
+                                    "peak": peak, "unit": "TFLOP/s",
+                                    "frac": flops / (ms / 1e3) / 1e12 / peak,
+                                    "peak_kind": "FP32 FMA lanes x max SM clock"}}
     plan.close()
     return wl
 

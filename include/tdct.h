@@ -213,6 +213,34 @@ int tdct_codec_error_batched_host(const tdct_plane* planes, int nplanes, const i
                                   size_t chunk_bytes, tdct_stream_t stream);
 
 /*
+ * tdct_ssim_batched -- mean structural similarity (MSSIM) of pairs of u8
+ * planes, the third figure of merit of §6.1, with the index as defined by
+ * Wang, Bovik, Sheikh and Simoncelli (2004), which §6.1 cites: an 11x11
+ * Gaussian window (standard deviation 1.5 samples, normalised to unit sum),
+ * K1 = 0.01, K2 = 0.03, L = 255, evaluated at every position where the window
+ * lies inside the plane (no padding) and averaged:
+ *   SSIM = ((2 mx my + C1)(2 sxy + C2)) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)).
+ * Typical use: x = an original plane, y = its reconstruction from the codec.
+ * Computed in FP32 (centred samples, separable window), accumulated in FP64;
+ * agrees with an FP64 evaluation of the definition to about 1e-6.
+ *   planes    host array of nplanes pairs (1 <= nplanes <= 2^20); x and y
+ *             are device pointers with row pitches in bytes; H, W >= 11
+ *   d_mssim   output, double [nplanes]
+ * Errors: TDCT_EINVAL (NULL pointer, H or W below 11, pitch below W,
+ * misaligned output), TDCT_ENOMEM, TDCT_ECUDA.
+ */
+typedef struct tdct_ssim_plane {
+  const void* x;   /* device pointer to sample (0, 0) of the reference plane */
+  int64_t x_pitch; /* row pitch in bytes */
+  const void* y;   /* device pointer to sample (0, 0) of the compared plane */
+  int64_t y_pitch; /* row pitch in bytes */
+  int32_t H, W;    /* size in samples, >= 11 */
+} tdct_ssim_plane;
+
+int tdct_ssim_batched(const tdct_ssim_plane* planes, int nplanes, double* d_mssim,
+                      tdct_stream_t stream);
+
+/*
  * Batch plans: the same work as tdct_codec_error_batched, prepared once
  * (validation, block-offset table in device memory, launch configuration)
  * and replayed as one CUDA graph per launch.  The plan owns its device

@@ -33,7 +33,7 @@ N1 = (8, 18, 20, 18, 8, 18, 20, 18)
 
 EXPORTS = (
     "tdct_forward", "tdct_zonal_inverse", "tdct_codec_error", "tdct_codec_error_batched",
-    "tdct_codec_error_batched_noalloc", "tdct_codec_error_batched_host",
+    "tdct_codec_error_batched_noalloc", "tdct_codec_error_batched_host", "tdct_ssim_batched",
     "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_config",
     "tdct_plan_destroy",
     "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_codec_error_batched.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp]
     L.tdct_codec_error_batched_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
     L.tdct_codec_error_batched_host.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.tdct_ssim_batched.argtypes = [vp, i32, vp, vp]
     L.tdct_plan_create.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_void_p)]
     L.tdct_plan_launch.argtypes = [vp, vp, vp, vp]
     L.tdct_plan_kernel_count.argtypes = [vp]
@@ -219,6 +220,28 @@ def tdct_codec_error_batched_host(planes, sse, psnr=None, T=None, n=None, chunk_
     _check(load().tdct_codec_error_batched_host(ctypes.addressof(planes), len(planes), tb, nb,
                                                 _ptr(sse), _ptr(psnr), int(chunk_bytes),
                                                 _stream(stream)))
+
+
+class TdctSsimPlane(ctypes.Structure):
+    _fields_ = [
+        ("x", ctypes.c_void_p), ("x_pitch", ctypes.c_int64),
+        ("y", ctypes.c_void_p), ("y_pitch", ctypes.c_int64),
+        ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+    ]
+
+
+def tdct_ssim_batched(pairs, mssim, stream=None) -> None:
+    """Mean SSIM of each (x, y) pair of 2-D uint8 device tensors into the
+    float64 device tensor ``mssim``."""
+    arr = (TdctSsimPlane * len(pairs))()
+    for i, (x, y) in enumerate(pairs):
+        _, H, W, xp = _plane_info(x)
+        _, Hy, Wy, yp = _plane_info(y)
+        if (H, W) != (Hy, Wy):
+            raise ValueError("SSIM pairs need equal shapes")
+        arr[i] = TdctSsimPlane(_ptr(x), xp, _ptr(y), yp, H, W)
+    _check(load().tdct_ssim_batched(ctypes.addressof(arr), len(pairs), _ptr(mssim),
+                                    _stream(stream)))
 
 
 class TdctPlan:

@@ -26,6 +26,7 @@
 #include "tdct_dct.h"
 #include "tdct_generic.cuh"
 #include "tdct_kernels.cuh"
+#include "tdct_ssim.h"
 #include "tdct_tc.h"
 
 namespace tdct {
@@ -1129,6 +1130,61 @@ int tdct_codec_error_batched_host(const tdct_plane* planes, int nplanes, const i
                 bad_plane >= 0 ? " of plane " : "",
                 bad_plane >= 0 ? std::to_string(bad_plane).c_str() : "", cudaGetErrorString(e));
   if (ew != cudaSuccess) return cuda_fail(ew, "tdct_codec_error_batched_host: stream join");
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  return TDCT_OK;
+}
+
+int tdct_ssim_batched(const tdct_ssim_plane* planes, int nplanes, double* d_mssim,
+                      tdct_stream_t stream) {
+  if (!planes || nplanes < 1 || nplanes > (1 << 20))
+    return fail(TDCT_EINVAL, "nplanes = %d outside 1..2^20 (or planes is NULL)", nplanes);
+  if (!d_mssim || (reinterpret_cast<uintptr_t>(d_mssim) & 7))
+    return fail(TDCT_EINVAL, "d_mssim NULL or not 8-byte aligned");
+  std::vector<SsimDesc> descs(nplanes);
+  int64_t units = 0;
+  for (int i = 0; i < nplanes; ++i) {
+    const tdct_ssim_plane& p = planes[i];
+    if (!p.x || !p.y) return fail(TDCT_EINVAL, "plane %d: NULL plane pointer", i);
+    if (p.H < kSsimWin || p.W < kSsimWin || p.H > (1 << 28) || p.W > (1 << 28))
+      return fail(TDCT_EINVAL, "plane %d: size %d x %d (SSIM needs at least 11 x 11)", i, p.H,
+                  p.W);
+    if (p.x_pitch < p.W || p.y_pitch < p.W)
+      return fail(TDCT_EINVAL, "plane %d: pitch below W", i);
+    SsimDesc& d = descs[i];
+    std::memset(&d, 0, sizeof d);
+    d.x = static_cast<const uint8_t*>(p.x);
+    d.y = static_cast<const uint8_t*>(p.y);
+    d.xpitch = p.x_pitch;
+    d.ypitch = p.y_pitch;
+    d.H = p.H;
+    d.W = p.W;
+    d.strips = (p.W - (kSsimWin - 1) + kSsimStrip - 1) / kSsimStrip;
+    d.bands = (p.H - (kSsimWin - 1) + kSsimBand - 1) / kSsimBand;
+    d.unit_begin = units;
+    d.slot = i;
+    units += (int64_t)d.strips * d.bands;
+  }
+  // window of Wang et al. (2004): g_j = exp(-(j - 5)^2 / (2 * 1.5^2)), unit sum
+  SsimParams sp;
+  double g[kSsimWin], gs = 0.0;
+  for (int j = 0; j < kSsimWin; ++j) {
+    const double t = j - (kSsimWin - 1) / 2;
+    g[j] = std::exp(-t * t / (2.0 * 1.5 * 1.5));
+    gs += g[j];
+  }
+  for (int j = 0; j < kSsimWin; ++j) sp.g[j] = (float)(g[j] / gs);
+  sp.C1 = (float)((0.01 * 255.0) * (0.01 * 255.0));
+  sp.C2 = (float)((0.03 * 255.0) * (0.03 * 255.0));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, sizeof(SsimDesc) * nplanes, s);
+  if (e != cudaSuccess) return fail(TDCT_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  SsimDesc* d_descs = static_cast<SsimDesc*>(scratch);
+  e = cudaMemcpyAsync(d_descs, descs.data(), sizeof(SsimDesc) * nplanes, cudaMemcpyHostToDevice,
+                      s);
+  if (e == cudaSuccess) e = launch_ssim(d_descs, nplanes, units, sp, d_mssim, s);
+  const cudaError_t ef = cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tdct_ssim_batched");
   if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
   return TDCT_OK;
 }

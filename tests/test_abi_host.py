@@ -200,3 +200,18 @@ def test_host_buffer_batch_rejects_before_any_cuda_call():
     planes = P.make_planes_raw([(None, 64, 16, 64, 10, 0, 0, 0)])
     assert L.tdct_codec_error_batched_host(ctypes.addressof(planes), 1, tb, nb, FAKE, None, 0,
                                            None) == _lib.TDCT_EINVAL
+
+
+def test_ssim_rejects_before_any_cuda_call():
+    L = P.load()
+    good = _lib.TdctSsimPlane(FAKE, 64, FAKE, 64, 16, 64)
+    small = _lib.TdctSsimPlane(FAKE, 64, FAKE, 64, 10, 64)
+    arr = (_lib.TdctSsimPlane * 2)(good, small)
+    assert L.tdct_ssim_batched(ctypes.addressof(arr), 2, FAKE, None) == _lib.TDCT_EINVAL
+    assert "plane 1" in L.tdct_last_error().decode()
+    arr = (_lib.TdctSsimPlane * 1)(_lib.TdctSsimPlane(None, 64, FAKE, 64, 16, 64))
+    assert L.tdct_ssim_batched(ctypes.addressof(arr), 1, FAKE, None) == _lib.TDCT_EINVAL
+    arr = (_lib.TdctSsimPlane * 1)(_lib.TdctSsimPlane(FAKE, 63, FAKE, 64, 16, 64))
+    assert L.tdct_ssim_batched(ctypes.addressof(arr), 1, FAKE, None) == _lib.TDCT_EINVAL
+    arr = (_lib.TdctSsimPlane * 1)(good)
+    assert L.tdct_ssim_batched(ctypes.addressof(arr), 1, FAKE + 4, None) == _lib.TDCT_EINVAL
