@@ -150,3 +150,67 @@ def search_all_orders(P: tuple = P2, tie: str = "small"):
     walk([], rows, base, {})
     out.sort(key=lambda x: x[0])
     return out
+
+
+# ---- the same search for any blocklength N ---------------------------------------
+#
+# §6.2 extends the question to N = 16 (search space P^16, 3^16 candidates for
+# P = {-1, 0, 1}) and times one fixed row sequence.  ``abm_approx_n`` is the
+# search above written for any N and any alphabet, with the same readings
+# (pairwise orthogonality, zero vector excluded, cosines in FP64 with the
+# TIE_TOL tolerance, the norm policy, then the enumeration order).  Candidates
+# are enumerated as base-|P| numbers over sorted(P), first coordinate most
+# significant: the order of ``search_space``.  Plain vectorised evaluation in
+# chunks; no pruning.
+
+def candidate_block(P: tuple, N: int, start: int, stop: int) -> np.ndarray:
+    """Candidates start..stop-1 of the full enumeration of P^N (zero vector
+    included), as an int8 array of shape (stop - start, N)."""
+    vals = np.array(sorted(P), dtype=np.int8)
+    idx = np.arange(start, stop, dtype=np.int64)
+    base = len(vals)
+    out = np.empty((stop - start, N), dtype=np.int8)
+    for pos in range(N - 1, -1, -1):
+        out[:, pos] = vals[idx % base]
+        idx //= base
+    return out
+
+
+def abm_approx_n(N: int, order, P: tuple, tie: str = "small", fixed=None,
+                 chunk: int = 1 << 22):
+    """Greedy search for blocklength N over P^N for the row order ``order``
+    (0-based rows of the N-point DCT), with ``fixed`` = {row: vector} preset.
+    Returns the N x N int64 matrix (rows not in ``order`` or ``fixed`` stay
+    zero), or None when a row has no orthogonal candidate left."""
+    C = dct_matrix(N)
+    total = len(P) ** N
+    T = np.zeros((N, N), dtype=np.int64)
+    chosen = []
+    for row, vec in (fixed or {}).items():
+        T[row] = vec
+        chosen.append(np.asarray(vec, dtype=np.int64))
+    for row in order:
+        cos_all = np.full(total, -np.inf)
+        norm2_all = np.zeros(total, dtype=np.int64)
+        for s in range(0, total, chunk):
+            e = min(total, s + chunk)
+            D = candidate_block(P, N, s, e).astype(np.int64)
+            n2 = np.einsum("ij,ij->i", D, D)
+            ok = n2 > 0
+            for t in chosen:
+                ok &= (D @ t) == 0
+            cos = np.full(e - s, -np.inf)
+            cos[ok] = (D[ok].astype(np.float64) @ C[row]) / np.sqrt(n2[ok])
+            cos_all[s:e] = cos
+            norm2_all[s:e] = n2
+        best = cos_all.max()
+        if not np.isfinite(best):
+            return None
+        ties = np.nonzero(cos_all >= best - TIE_TOL)[0]
+        if len(ties) > 1:
+            n2 = norm2_all[ties]
+            ties = ties[n2 == (n2.min() if tie == "small" else n2.max())]
+        v = candidate_block(P, N, int(ties[0]), int(ties[0]) + 1)[0].astype(np.int64)
+        T[row] = v
+        chosen.append(v)
+    return T

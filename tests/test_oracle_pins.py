@@ -438,3 +438,54 @@ def test_ssim_luminance_shift_leaves_only_the_luminance_term():
 def test_ssim_needs_a_full_window():
     with pytest.raises(ValueError):
         oc.ssim_plane(np.zeros((10, 40), np.uint8), np.zeros((10, 40), np.uint8))
+
+
+# ---- the search for any blocklength (§6.2 asks it for N = 16) -------------------------
+
+
+@pytest.mark.parametrize("P", [S.P1, S.P2])
+@pytest.mark.parametrize("tie", ["small", "large"])
+def test_search_any_N_reduces_to_the_8_point_search(P, tie):
+    rng = np.random.default_rng(5)
+    orders = [tuple(int(v) for v in rng.permutation([2, 3, 4, 6, 7, 8])) for _ in range(6)]
+    for order in orders:
+        a = S.abm_approx(order, P, tie, {1: S.ROW1, 5: S.ROW5})
+        b = S.abm_approx_n(8, [o - 1 for o in order], P, tie, {0: S.ROW1, 4: S.ROW5})
+        assert (a is None and b is None) or np.array_equal(a, b), order
+
+
+def _brute_force_search(N, order, P, tie):
+    """Pure-Python restatement: every candidate of P^N in lexicographic order
+    over sorted(P), cosines with math.fsum, the same tie rules."""
+    import itertools
+    import math
+
+    C = [[(math.sqrt(1.0 / N) if k == 0 else math.sqrt(2.0 / N)) *
+          math.cos(math.pi * (2 * j + 1) * k / (2 * N)) for j in range(N)] for k in range(N)]
+    cands = [d for d in itertools.product(sorted(P), repeat=N) if any(d)]
+    chosen, T = [], [[0] * N for _ in range(N)]
+    for row in order:
+        ok = [d for d in cands if all(sum(a * b for a, b in zip(d, t)) == 0 for t in chosen)]
+        if not ok:
+            return None
+        cos = [math.fsum(C[row][j] * d[j] for j in range(N)) / math.sqrt(sum(v * v for v in d))
+               for d in ok]
+        best = max(cos)
+        ties = [d for d, c in zip(ok, cos) if c >= best - S.TIE_TOL]
+        n2 = [sum(v * v for v in d) for d in ties]
+        want = min(n2) if tie == "small" else max(n2)
+        pick = [d for d, n in zip(ties, n2) if n == want][0]
+        T[row] = list(pick)
+        chosen.append(pick)
+    return np.array(T, dtype=np.int64)
+
+
+@pytest.mark.parametrize("N,P", [(4, S.P1), (4, S.P2), (5, S.P1)])
+def test_search_any_N_matches_brute_force_on_every_order(N, P):
+    import itertools
+
+    for order in itertools.permutations(range(N)):
+        for tie in ("small", "large"):
+            want = _brute_force_search(N, order, P, tie)
+            got = S.abm_approx_n(N, order, P, tie)
+            assert (want is None and got is None) or np.array_equal(got, want), (order, tie)
