@@ -52,6 +52,8 @@ def parse():
                     help="the 8-point matrix (T1: fused kernels; others: generic kernels)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-search", action="store_true",
+                    help="skip the angle-search timing (N = 16 and N = 12, P = {-1, 0, 1})")
     ap.add_argument("--no-ssim", action="store_true",
                     help="skip the MSSIM measurement (originals vs reconstructions)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -399,6 +401,40 @@ def time_ours(args, dist, out):
     return wl
 
 
+def time_search(skip_cpu: bool):
+    """The greedy angle search on the GPU for one row order (natural order,
+    P = {-1, 0, 1}) at N = 16, the case §6.2 times at about 6 minutes on a
+    16-core Xeon E5-2630 v3, and at N = 12 with the CPU oracle beside it."""
+    import numpy as np
+    import torch
+
+    import paper_1808_02950_gb300 as P
+
+    res = {"alphabet": [-1, 0, 1], "order": "natural (rows 0..N-1)"}
+    for N in (16, 12):
+        P.tdct_search(N, (-1, 0, 1), range(N))  # warm-up (module load, pool)
+        ts = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            T, complete = P.tdct_search(N, (-1, 0, 1), range(N))
+            ts.append(time.perf_counter() - t0)
+        rows = int(np.count_nonzero(np.abs(np.array(T)).sum(axis=1)))
+        res[f"N{N}"] = {"ms": 1e3 * statistics.median(ts), "rows_found": rows,
+                        "complete": complete, "candidates": 3 ** N - 1}
+    res["N16"]["paper_cpu_seconds"] = 360.0
+    res["N16"]["paper_cpu"] = "16-core Xeon E5-2630 v3 @ 2.4 GHz (§6.2, row sequence not stated)"
+    if not skip_cpu:
+        from oracle import search as S
+
+        t0 = time.perf_counter()
+        S.abm_approx_n(12, range(12), S.P1, "small")
+        cpu_s = time.perf_counter() - t0
+        res["N12"]["cpu_baseline"] = {"seconds": cpu_s, "kind": "oracle", "cores": 1,
+                                      "sample": "the whole N = 12 natural-order search, numpy"}
+    return res
+
+
 def oracle_matrix(name: str):
     from oracle import matrices as M
 
@@ -461,6 +497,8 @@ def main():
     dist = Dist(backend)
     out = {}
     wl = time_ours(args, dist, out)
+    if dist.rank == 0 and not args.no_search:
+        out["search"] = time_search(args.no_cpu_baseline or dist.world > 1)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         sample = host_sample(wl, 256)
         rate, nb, cores, npl = cpu_oracle_rate(sample, args.cpu_seconds, args.transform)

@@ -241,6 +241,37 @@ int tdct_ssim_batched(const tdct_ssim_plane* planes, int nplanes, double* d_mssi
                       tdct_stream_t stream);
 
 /*
+ * tdct_search -- the greedy angle search of §3 (Eq. (6); §6.2 poses it for
+ * N = 16) on the GPU, for one row order.  Candidates are the vectors of
+ * P^N (P = `alphabet`), enumerated as base-|P| numbers over the sorted
+ * alphabet with the first coordinate most significant; the zero vector is
+ * not a candidate.  For each row k of `order` in turn, the candidate with the
+ * largest cos(c_k, d) = <c_k, d> / ||d|| (c_k = row k of the orthonormal
+ * N-point DCT-II, FP64) among those orthogonal to every preset and every
+ * row already chosen becomes row k.  Cosines within 1e-12 of the maximum
+ * tie; `tie` 0 keeps the smaller-norm vector, 1 the larger, then the first
+ * in the enumeration.
+ *   N           blocklength, 2..16
+ *   alphabet    np distinct values in [-127, 127], 2 <= np <= 9,
+ *               np^N <= 2^31
+ *   order       n_order distinct rows (0-based), searched in this order
+ *   fixed_rows  n_fixed distinct preset rows (0-based; not in `order`),
+ *               fixed_vals their n_fixed x N entries (row-major); both may be
+ *               NULL when n_fixed = 0
+ *   T_out       host output, int8 [N][N]: searched and preset rows; rows not
+ *               reached stay 0
+ *   complete    host output: 1, or 0 when some row had no orthogonal
+ *               candidate left (the rows before it are in T_out)
+ * Synchronous: the call waits for its work on `stream`.  Device scratch of
+ * 8 np^N bytes comes from the stream-ordered pool.
+ * Errors: TDCT_EINVAL (arguments), TDCT_EUNSUPPORTED (np^N > 2^31),
+ * TDCT_ENOMEM, TDCT_ECUDA.
+ */
+int tdct_search(int N, const int8_t* alphabet, int np, const int32_t* order, int n_order,
+                const int32_t* fixed_rows, const int8_t* fixed_vals, int n_fixed, int tie,
+                int8_t* T_out, int32_t* complete, tdct_stream_t stream);
+
+/*
  * Batch plans: the same work as tdct_codec_error_batched, prepared once
  * (validation, block-offset table in device memory, launch configuration)
  * and replayed as one CUDA graph per launch.  The plan owns its device

@@ -34,6 +34,7 @@ N1 = (8, 18, 20, 18, 8, 18, 20, 18)
 EXPORTS = (
     "tdct_forward", "tdct_zonal_inverse", "tdct_codec_error", "tdct_codec_error_batched",
     "tdct_codec_error_batched_noalloc", "tdct_codec_error_batched_host", "tdct_ssim_batched",
+    "tdct_search",
     "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_config",
     "tdct_plan_destroy",
     "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
@@ -80,6 +81,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_codec_error_batched_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
     L.tdct_codec_error_batched_host.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.tdct_ssim_batched.argtypes = [vp, i32, vp, vp]
+    L.tdct_search.argtypes = [i32, vp, i32, vp, i32, vp, vp, i32, i32, vp, vp, vp]
     L.tdct_plan_create.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_void_p)]
     L.tdct_plan_launch.argtypes = [vp, vp, vp, vp]
     L.tdct_plan_kernel_count.argtypes = [vp]
@@ -242,6 +244,26 @@ def tdct_ssim_batched(pairs, mssim, stream=None) -> None:
         arr[i] = TdctSsimPlane(_ptr(x), xp, _ptr(y), yp, H, W)
     _check(load().tdct_ssim_batched(ctypes.addressof(arr), len(pairs), _ptr(mssim),
                                     _stream(stream)))
+
+
+def tdct_search(N: int, alphabet, order, fixed=None, tie: str = "small", stream=None):
+    """The greedy angle search for one row order on the GPU.  ``order``:
+    0-based rows searched in turn; ``fixed``: {row: vector} presets.
+    Returns (T as an N x N list of lists, complete)."""
+    alph = (ctypes.c_int8 * len(alphabet))(*[int(v) for v in alphabet])
+    order = list(order)
+    ordb = (ctypes.c_int32 * len(order))(*order)
+    fixed = fixed or {}
+    frows = (ctypes.c_int32 * max(1, len(fixed)))(*list(fixed.keys()))
+    fvals = (ctypes.c_int8 * max(1, N * len(fixed)))(*[int(v) for row in fixed.values()
+                                                        for v in row])
+    T = (ctypes.c_int8 * (N * N))()
+    complete = ctypes.c_int32(0)
+    _check(load().tdct_search(N, alph, len(alphabet), ordb, len(order),
+                              frows if fixed else None, fvals if fixed else None, len(fixed),
+                              {"small": 0, "large": 1}[tie], T, ctypes.byref(complete),
+                              _stream(stream)))
+    return [[T[i * N + j] for j in range(N)] for i in range(N)], bool(complete.value)
 
 
 class TdctPlan:

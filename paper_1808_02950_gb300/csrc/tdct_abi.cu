@@ -26,6 +26,7 @@
 #include "tdct_dct.h"
 #include "tdct_generic.cuh"
 #include "tdct_kernels.cuh"
+#include "tdct_search.h"
 #include "tdct_ssim.h"
 #include "tdct_tc.h"
 
@@ -1186,6 +1187,89 @@ int tdct_ssim_batched(const tdct_ssim_plane* planes, int nplanes, double* d_mssi
   const cudaError_t ef = cudaFreeAsync(scratch, s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_ssim_batched");
   if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  return TDCT_OK;
+}
+
+int tdct_search(int N, const int8_t* alphabet, int np, const int32_t* order, int n_order,
+                const int32_t* fixed_rows, const int8_t* fixed_vals, int n_fixed, int tie,
+                int8_t* T_out, int32_t* complete, tdct_stream_t stream) {
+  if (N < 2 || N > kSearchMaxN) return fail(TDCT_EINVAL, "N = %d outside 2..16", N);
+  if (!alphabet || np < 2 || np > 9) return fail(TDCT_EINVAL, "alphabet of %d values", np);
+  if (!order || n_order < 1 || n_order > N) return fail(TDCT_EINVAL, "n_order = %d", n_order);
+  if (n_fixed < 0 || n_fixed + n_order > N || (n_fixed > 0 && (!fixed_rows || !fixed_vals)))
+    return fail(TDCT_EINVAL, "n_fixed = %d (or NULL presets)", n_fixed);
+  if (tie != 0 && tie != 1) return fail(TDCT_EINVAL, "tie = %d is neither 0 nor 1", tie);
+  if (!T_out || !complete) return fail(TDCT_EINVAL, "T_out and complete must not be NULL");
+  SearchParams sp;
+  std::memset(&sp, 0, sizeof sp);
+  std::vector<int> vals(alphabet, alphabet + np);
+  std::sort(vals.begin(), vals.end());
+  for (int a = 0; a < np; ++a) {
+    if (vals[a] < -127) return fail(TDCT_EINVAL, "alphabet value %d below -127", vals[a]);
+    if (a > 0 && vals[a] == vals[a - 1]) return fail(TDCT_EINVAL, "alphabet repeats %d", vals[a]);
+    sp.alphabet[a] = vals[a];
+  }
+  uint64_t total = 1;
+  for (int k = 0; k < N; ++k) {
+    total *= (uint64_t)np;
+    if (total > (1ull << 31)) return fail(TDCT_EUNSUPPORTED, "np^N above 2^31 candidates");
+  }
+  std::vector<int> used(N, 0);
+  for (int f = 0; f < n_fixed; ++f) {
+    const int r = fixed_rows[f];
+    if (r < 0 || r >= N || used[r]) return fail(TDCT_EINVAL, "preset row %d", r);
+    used[r] = 1;
+    for (int k = 0; k < N; ++k) sp.fixed[f][k] = fixed_vals[f * N + k];
+  }
+  for (int i = 0; i < n_order; ++i) {
+    const int r = order[i];
+    if (r < 0 || r >= N || used[r]) return fail(TDCT_EINVAL, "order entry %d (row %d)", i, r);
+    used[r] = 1;
+  }
+  sp.np = np;
+  sp.N = N;
+  sp.total = (uint32_t)total;
+  sp.n_fixed = n_fixed;
+  sp.tie_large = tie;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* block = nullptr;
+  const size_t bytes_cos = round_up(sizeof(double) * (size_t)total, 256);
+  cudaError_t e = cudaMallocAsync(&block, bytes_cos + sizeof(SearchState), s);
+  if (e != cudaSuccess) return fail(TDCT_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
+  double* cosv = static_cast<double*>(block);
+  SearchState* st = reinterpret_cast<SearchState*>(static_cast<char*>(block) + bytes_cos);
+  SearchState init;
+  std::memset(&init, 0, sizeof init);
+  init.pick_key = ~0ull;
+  e = cudaMemcpyAsync(st, &init, sizeof init, cudaMemcpyHostToDevice, s);
+  for (int i = 0; i < n_order && e == cudaSuccess; ++i) {
+    // exact row of the orthonormal N-point DCT-II, coordinates reversed
+    const int k = order[i];
+    for (int j = 0; j < kSearchMaxN; ++j) sp.crow_rev[j] = 0.0;
+    for (int j = 0; j < N; ++j) {
+      const double ck = k == 0 ? std::sqrt(1.0 / N) : std::sqrt(2.0 / N);
+      sp.crow_rev[N - 1 - j] = ck * std::cos(M_PI * (2.0 * j + 1.0) * k / (2.0 * N));
+    }
+    e = enqueue_search_row(sp, st, cosv, i == 0, i, s);
+  }
+  SearchState out;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&out, st, sizeof out, cudaMemcpyDeviceToHost, s);
+  const cudaError_t ef = cudaFreeAsync(block, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "tdct_search");
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  std::memset(T_out, 0, (size_t)N * N);
+  for (int f = 0; f < n_fixed; ++f)
+    for (int k = 0; k < N; ++k) T_out[fixed_rows[f] * N + k] = fixed_vals[f * N + k];
+  // the rows committed before a dead end (all of them otherwise)
+  for (int i = 0; i < out.n_done && i < n_order; ++i) {
+    uint32_t idx = out.chosen[i];
+    for (int k = N - 1; k >= 0; --k) {
+      T_out[order[i] * N + k] = (int8_t)vals[idx % np];
+      idx /= np;
+    }
+  }
+  *complete = out.dead ? 0 : 1;
   return TDCT_OK;
 }
 

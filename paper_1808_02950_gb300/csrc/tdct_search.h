@@ -1,0 +1,38 @@
+// tdct_search.h -- GPU greedy angle search (internal interface).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace tdct {
+
+constexpr int kSearchMaxN = 16;
+constexpr double kSearchTieTol = 1e-12;
+
+struct SearchParams {
+  double crow_rev[kSearchMaxN];         // exact DCT row, coordinates reversed, zero past N
+  int32_t alphabet[9];                  // sorted, distinct
+  int32_t np;                           // alphabet size
+  int32_t N;
+  uint32_t total;                       // np^N candidates (zero vector included)
+  int32_t n_fixed;
+  int32_t tie_large;                    // 0: smaller norm first, 1: larger
+  int8_t fixed[kSearchMaxN][kSearchMaxN];  // preset rows (coordinate order)
+};
+
+struct SearchState {
+  unsigned long long best_key;  // order-preserving key of the best cosine (0 = none yet)
+  unsigned long long pick_key;  // (norm key << 32) | index of the winner (~0 = none yet)
+  int32_t dead;                 // a row had no allowed candidate
+  int32_t n_done;               // rows committed so far
+  int8_t last_row[kSearchMaxN];
+  uint32_t chosen[kSearchMaxN];  // winner index per searched row
+};
+
+// Enqueue the max / pick / commit launches of one searched row.  `first`:
+// test against the presets (and start from all candidates); later rows test
+// against the row chosen last and skip candidates already rejected in cosv.
+cudaError_t enqueue_search_row(const SearchParams& sp, SearchState* st, double* cosv, int first,
+                               int slot, cudaStream_t s);
+
+}  // namespace tdct

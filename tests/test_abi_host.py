@@ -215,3 +215,22 @@ def test_ssim_rejects_before_any_cuda_call():
     assert L.tdct_ssim_batched(ctypes.addressof(arr), 1, FAKE, None) == _lib.TDCT_EINVAL
     arr = (_lib.TdctSsimPlane * 1)(good)
     assert L.tdct_ssim_batched(ctypes.addressof(arr), 1, FAKE + 4, None) == _lib.TDCT_EINVAL
+
+
+def test_search_rejects_before_any_cuda_call():
+    L = P.load()
+    alph = (ctypes.c_int8 * 3)(0, 1, -1)
+    order = (ctypes.c_int32 * 2)(0, 1)
+    T = (ctypes.c_int8 * 64)()
+    c = ctypes.c_int32()
+    ok = lambda *a: L.tdct_search(*a)
+    assert ok(1, alph, 3, order, 2, None, None, 0, 0, T, ctypes.byref(c), None) == _lib.TDCT_EINVAL
+    assert ok(8, alph, 1, order, 2, None, None, 0, 0, T, ctypes.byref(c), None) == _lib.TDCT_EINVAL
+    dup = (ctypes.c_int8 * 3)(0, 1, 1)
+    assert ok(8, dup, 3, order, 2, None, None, 0, 0, T, ctypes.byref(c), None) == _lib.TDCT_EINVAL
+    bad = (ctypes.c_int32 * 2)(0, 0)
+    assert ok(8, alph, 3, bad, 2, None, None, 0, 0, T, ctypes.byref(c), None) == _lib.TDCT_EINVAL
+    assert ok(8, alph, 3, order, 2, None, None, 0, 2, T, ctypes.byref(c), None) == _lib.TDCT_EINVAL
+    big = (ctypes.c_int8 * 9)(*range(-4, 5))
+    assert ok(16, big, 9, order, 2, None, None, 0, 0, T, ctypes.byref(c), None) \
+        == _lib.TDCT_EUNSUPPORTED
