@@ -78,6 +78,12 @@ def lib() -> ctypes.CDLL:
                                      ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_double)]
         L.orc_ssim_plane.restype = ctypes.c_int
+        L.orc_codec_plane_b.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_int64, i64p]
+        L.orc_codec_plane_b.restype = ctypes.c_int
+        L.orc_zigzag_b.argtypes = [ctypes.c_int, i32p]
+        L.orc_zigzag_b.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -172,6 +178,30 @@ def dct_codec_plane(img: np.ndarray, r: int, want_recon: bool = True, want_coef:
     if rc != 0:
         raise ValueError(f"oracle dct_codec_plane failed with code {rc}")
     return sse.value, recon, coef
+
+
+def codec_plane_b(img: np.ndarray, T, B: int, r: int, want_recon: bool = True):
+    """The codec with B x B blocks (B = 8, 16, 32) and the B x B matrix T.
+    Returns (sse, recon or None)."""
+    img, dtype, H, W, pitch = _plane_args(img)
+    T = np.ascontiguousarray(np.asarray(T), dtype=np.int32)
+    assert T.shape == (B, B)
+    recon = np.zeros_like(img) if want_recon else None
+    sse = ctypes.c_int64(0)
+    rc = lib().orc_codec_plane_b(img.ctypes.data, pitch, H, W, dtype, B,
+                                 _ptr(T, ctypes.c_int32), r,
+                                 recon.ctypes.data if recon is not None else None,
+                                 recon.strides[0] if recon is not None else 0, ctypes.byref(sse))
+    if rc != 0:
+        raise ValueError(f"orc_codec_plane_b failed ({rc})")
+    return sse.value, recon
+
+
+def zigzag_b(B: int) -> np.ndarray:
+    """Scan index of every position (i, j) of a B x B block, as a B x B array."""
+    out = np.zeros(B * B, np.int32)
+    assert lib().orc_zigzag_b(B, _ptr(out, ctypes.c_int32)) == 0
+    return out.reshape(B, B)
 
 
 def ssim_plane(x: np.ndarray, y: np.ndarray) -> float:

@@ -236,6 +236,51 @@ def row_norms_sq(T: np.ndarray) -> np.ndarray:
     return np.einsum("ij,ij->i", T, T)
 
 
+def jam(T_half: np.ndarray, lower_add: str = "I,-Ibar") -> np.ndarray:
+    """The JAM step of §6.2, Eq. (jam), without its 1/sqrt(2) (merged into the
+    scaling): T_(N) = M_per [T_(N/2) 0; 0 T_(N/2)] M_add.
+
+    M_per is built from P_{N-1, N/2}, whose even rows i are row i/2 of the
+    identity and odd rows zero; its printed block layout places the
+    (N-1) x (N/2) block P beside a 1 x (N/2) zero block, read here as block
+    columns [P; 0] and [0; P]: the N x N permutation taking row 2i from the
+    first copy of T_(N/2) and row 2i + 1 from the second.
+
+    M_add's upper block row is [I, Ibar] (Ibar the counter-identity).  Its
+    printed lower block row [Ibar, -I] does not give the matrices the paper
+    prints after the recursion; [I, -Ibar] does (the two differ only in the
+    signs of the rows built from antisymmetric rows of T_(N/2), which leaves
+    the codec's reconstruction unchanged).  ``lower_add`` selects "I,-Ibar"
+    (default, the printed matrices) or "Ibar,-I" (the printed formula)."""
+    T_half = np.asarray(T_half, dtype=np.int64)
+    h = T_half.shape[0]
+    N = 2 * h
+    I = np.eye(h, dtype=np.int64)
+    Ibar = I[::-1]
+    lower = np.hstack([I, -Ibar]) if lower_add == "I,-Ibar" else np.hstack([Ibar, -I])
+    M_add = np.vstack([np.hstack([I, Ibar]), lower])
+    P = np.zeros((N - 1, h), dtype=np.int64)
+    for i in range(0, N - 1, 2):
+        P[i] = I[i // 2]
+    z = np.zeros((1, h), dtype=np.int64)
+    M_per = np.hstack([np.vstack([P, z]), np.vstack([z, P])])
+    blk = np.block([[T_half, np.zeros((h, h), np.int64)], [np.zeros((h, h), np.int64), T_half]])
+    return M_per @ blk @ M_add
+
+
+def jam_cost(N: int) -> tuple[int, int]:
+    """(additions, shifts) of the JAM transform from T1 (§6.2): twice the
+    half-size transform's counts plus N additions for M_add; T1 itself has
+    24 additions and 6 shifts (§5.1)."""
+    if N == 8:
+        return 24, 6
+    a, s = jam_cost(N // 2)
+    return 2 * a + N, 2 * s
+
+
+T16 = jam(T1)
+T32 = jam(T16)
+
 NAMED = {
     "T1": T1,
     "T2": T2,

@@ -391,3 +391,126 @@ int orc_ssim_plane(const uint8_t* x, int64_t xpitch, const uint8_t* y, int64_t y
   *mssim = total / ((double)(H - WIN + 1) * (double)(W - WIN + 1));
   return ORC_OK;
 }
+
+/*
+ * The codec of §6.1 for B x B blocks (B = 8, 16 or 32; §6.2 builds the 16-
+ * and 32-point matrices with the JAM recursion), for any integer T with
+ * orthogonal rows, by the definitions above written for B:
+ *   Z = T X T^T (int64), keep the first r positions of the B x B zig-zag
+ *   scan (anti-diagonals, odd ones from (0, s) with i increasing, even ones
+ *   from (s, 0) with i decreasing), N = T^T (M o Z o q q^T) T with q = L / n,
+ *   L = lcm(n), x' = sign(N) floor((|N| + L^2/2) / L^2), clamped.
+ * Magnitudes stay in int64: |Z| < 2^20 and |N| < 2^43 for B = 32.
+ */
+static void zigzag_b(int B, int32_t* index_of_pos) {
+  int idx = 0;
+  for (int s = 0; s <= 2 * B - 2; ++s) {
+    if (s % 2 == 1) {
+      for (int i = 0; i <= s; ++i) {
+        const int j = s - i;
+        if (i < B && j < B) index_of_pos[i * B + j] = idx++;
+      }
+    } else {
+      for (int i = s; i >= 0; --i) {
+        const int j = s - i;
+        if (i < B && j < B) index_of_pos[i * B + j] = idx++;
+      }
+    }
+  }
+}
+
+int orc_zigzag_b(int B, int32_t* index_of_pos) {
+  if (B < 1 || B > 64) return ORC_EINVAL;
+  zigzag_b(B, index_of_pos);
+  return ORC_OK;
+}
+
+int orc_codec_plane_b(const uint8_t* img, int64_t pitch, int H, int W, int dtype, int B,
+                      const int32_t* T, int r, uint8_t* recon, int64_t recon_pitch,
+                      int64_t* sse) {
+  if (!img || !sse || !T || H <= 0 || W <= 0 || (B != 8 && B != 16 && B != 32) || r < 1 ||
+      r > B * B || (dtype != 0 && dtype != 1))
+    return ORC_EINVAL;
+  const int BB = B * B;
+  int64_t* n = (int64_t*)malloc(sizeof(int64_t) * B);
+  int64_t* q = (int64_t*)malloc(sizeof(int64_t) * B);
+  int32_t* zz = (int32_t*)malloc(sizeof(int32_t) * BB);
+  int64_t* X = (int64_t*)malloc(sizeof(int64_t) * BB);
+  int64_t* Y = (int64_t*)malloc(sizeof(int64_t) * BB);
+  int64_t* Z = (int64_t*)malloc(sizeof(int64_t) * BB);
+  int rc = ORC_OK;
+  for (int a = 0; a < B && rc == ORC_OK; ++a)
+    for (int b = 0; b < B; ++b) {
+      int64_t dot = 0;
+      for (int l = 0; l < B; ++l) dot += (int64_t)T[a * B + l] * T[b * B + l];
+      if (a == b) {
+        if (dot <= 0) rc = ORC_ENOTORTHO;
+        n[a] = dot;
+      } else if (dot != 0) {
+        rc = ORC_ENOTORTHO;
+      }
+    }
+  if (rc == ORC_OK) {
+    int64_t L = n[0];
+    for (int i = 1; i < B; ++i) L = L / gcd64(L, n[i]) * n[i];
+    for (int i = 0; i < B; ++i) q[i] = L / n[i];
+    const int64_t L2 = L * L;
+    zigzag_b(B, zz);
+    const int64_t lo = dtype == 0 ? 0 : -255, hi = 255;
+    const int nby = (H + B - 1) / B, nbx = (W + B - 1) / B;
+    int64_t total = 0;
+    for (int by = 0; by < nby; ++by)
+      for (int bx = 0; bx < nbx; ++bx) {
+        for (int k = 0; k < B; ++k)
+          for (int l = 0; l < B; ++l) {
+            const int y = by * B + k, x = bx * B + l;
+            X[k * B + l] = (y < H && x < W) ? load_sample(img, pitch, dtype, y, x) : 0;
+          }
+        /* Y = T X, Z = Y T^T */
+        for (int i = 0; i < B; ++i)
+          for (int l = 0; l < B; ++l) {
+            int64_t acc = 0;
+            for (int k = 0; k < B; ++k) acc += (int64_t)T[i * B + k] * X[k * B + l];
+            Y[i * B + l] = acc;
+          }
+        for (int i = 0; i < B; ++i)
+          for (int j = 0; j < B; ++j) {
+            int64_t acc = 0;
+            for (int l = 0; l < B; ++l) acc += Y[i * B + l] * (int64_t)T[j * B + l];
+            Z[i * B + j] = zz[i * B + j] < r ? acc * q[i] * q[j] : 0;
+          }
+        /* V = T^T W (into Y), N = V T */
+        for (int k = 0; k < B; ++k)
+          for (int j = 0; j < B; ++j) {
+            int64_t acc = 0;
+            for (int i = 0; i < B; ++i) acc += (int64_t)T[i * B + k] * Z[i * B + j];
+            Y[k * B + j] = acc;
+          }
+        for (int k = 0; k < B; ++k)
+          for (int l = 0; l < B; ++l) {
+            int64_t N = 0;
+            for (int j = 0; j < B; ++j) N += Y[k * B + j] * (int64_t)T[j * B + l];
+            const int64_t a = N < 0 ? -N : N;
+            int64_t m = a / L2;
+            if (2 * (a - m * L2) >= L2) m += 1; /* half away from zero */
+            int64_t xr = N < 0 ? -m : m;
+            if (xr < lo) xr = lo;
+            if (xr > hi) xr = hi;
+            const int y = by * B + k, x = bx * B + l;
+            if (y < H && x < W) {
+              const int64_t d = X[k * B + l] - xr;
+              total += d * d;
+              if (recon) store_sample(recon, recon_pitch, dtype, y, x, xr);
+            }
+          }
+      }
+    *sse = total;
+  }
+  free(n);
+  free(q);
+  free(zz);
+  free(X);
+  free(Y);
+  free(Z);
+  return rc;
+}

@@ -489,3 +489,95 @@ def test_search_any_N_matches_brute_force_on_every_order(N, P):
             want = _brute_force_search(N, order, P, tie)
             got = S.abm_approx_n(N, order, P, tie)
             assert (want is None and got is None) or np.array_equal(got, want), (order, tie)
+
+
+# ---- §6.2: the 16- and 32-point matrices of the JAM recursion ---------------------------
+
+_JAM = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "jam_matrices.json")))
+
+
+def test_jam_reproduces_the_printed_16_and_32_point_matrices():
+    assert np.array_equal(M.T16, np.array(_JAM["T16"]))
+    assert np.array_equal(M.T32, np.array(_JAM["T32"]))
+
+
+def test_jam_diagonals_match_the_printed_kronecker_forms():
+    D16 = 4 * np.kron(np.eye(2), np.kron(np.diag([4, 9, 10, 9]), np.eye(2)))
+    D32 = 2 * np.kron(D16, np.eye(2))
+    assert np.array_equal(M.T16 @ M.T16.T, D16)   # orthogonal, and diag as printed
+    assert np.array_equal(M.T32 @ M.T32.T, D32)
+
+
+def test_jam_costs_match_table_9():
+    for N in ("8", "16", "32"):
+        c = _JAM["cost"][N]
+        assert M.jam_cost(int(N)) == (c["additions"], c["shifts"])
+
+
+def test_jam_printed_formula_differs_only_in_row_signs():
+    other = M.jam(M.T1, lower_add="Ibar,-I")
+    signs = np.sign(np.einsum("ij,ij->i", other, M.T16))
+    assert np.array_equal(np.abs(signs), np.ones(16))
+    assert np.array_equal(signs[:, None] * other, M.T16)
+    rng = np.random.default_rng(4)
+    x = rng.integers(0, 256, (32, 48)).astype(np.uint8)
+    for r in (1, 7, 40):
+        assert np.array_equal(oc.codec_plane_b(x, M.T16, 16, r)[1], oc.codec_plane_b(x, other, 16, r)[1])
+
+
+def test_zigzag_b_rule():
+    assert np.array_equal(oc.zigzag_b(8).reshape(-1), oc.zigzag()[1])
+    for B in (16, 32):
+        z = oc.zigzag_b(B)
+        assert sorted(z.reshape(-1).tolist()) == list(range(B * B))
+        assert (z[0, 0], z[0, 1], z[1, 0], z[2, 0], z[1, 1], z[0, 2]) == (0, 1, 2, 3, 4, 5)
+        s = np.add.outer(np.arange(B), np.arange(B))
+        assert all(z[s == a].max() < z[s == a + 1].min() for a in range(2 * B - 2))
+
+
+@pytest.mark.parametrize("B,T", [(16, M.T16), (32, M.T32)])
+def test_codec_b_lossless_mean_and_monotone(B, T):
+    rng = np.random.default_rng(B)
+    x = rng.integers(0, 256, (B + 5, 2 * B + 3)).astype(np.uint8)
+    assert oc.codec_plane_b(x, T, B, B * B)[0] == 0            # all coefficients kept
+    xb = x[:B, :B]
+    rec = oc.codec_plane_b(np.ascontiguousarray(xb), T, B, 1)[1]
+    mean = Fraction(int(xb.astype(np.int64).sum()), B * B)      # r = 1: the rounded block mean
+    want = int(mean.numerator * 2 + mean.denominator) // (2 * mean.denominator)
+    assert (rec == want).all()
+    sse = [oc.codec_plane_b(x, T, B, r, want_recon=False)[0] for r in (1, 4, 16, 64, 256)]
+    assert all(a >= b for a, b in zip(sse, sse[1:]))  # more kept coefficients, less error
+
+
+def test_codec_b_with_8_point_blocks_equals_the_8x8_codec():
+    rng = np.random.default_rng(8)
+    x = rng.integers(0, 256, (27, 35)).astype(np.uint8)
+    for r in (1, 10, 64):
+        a = oc.codec_plane_b(x, M.T1, 8, r)
+        b = oc.codec_plane(x, M.T1, r)
+        assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+def test_codec_b_exact_fractions_on_one_16x16_block():
+    """Brute force with exact rationals: B' = C_hat A C_hat^T, zonal, A' =
+    C_hat^T B' C_hat with C_hat = S T, rounded half away from zero."""
+    rng = np.random.default_rng(16)
+    X = rng.integers(0, 256, (16, 16))
+    T = M.T16.astype(object)
+    n = [int(v) for v in np.einsum("ij,ij->i", M.T16, M.T16)]
+    Z = T.dot(X.astype(object)).dot(T.T)
+    zz = oc.zigzag_b(16)
+    r = 23
+    W = [[Fraction(int(Z[i, j]), n[i] * n[j]) if zz[i, j] < r else Fraction(0)
+          for j in range(16)] for i in range(16)]
+    rec = np.zeros((16, 16), np.int64)
+    for k in range(16):
+        for l in range(16):
+            v = sum(W[i][j] * int(M.T16[i, k]) * int(M.T16[j, l]) for i in range(16) for j in range(16))
+            a = abs(v)
+            m = int(a)
+            if a - m >= Fraction(1, 2):
+                m += 1
+            rec[k, l] = min(max(m if v >= 0 else -m, 0), 255)
+    got = oc.codec_plane_b(X.astype(np.uint8), M.T16, 16, r)[1]
+    assert np.array_equal(got, rec)
