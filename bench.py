@@ -52,6 +52,8 @@ def parse():
                     help="the 8-point matrix (T1: fused kernels; others: generic kernels)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-jam", action="store_true",
+                    help="skip the 16x16 / 32x32 JAM codec timing")
     ap.add_argument("--no-search", action="store_true",
                     help="skip the angle-search timing (N = 16 and N = 12, P = {-1, 0, 1})")
     ap.add_argument("--no-ssim", action="store_true",
@@ -397,8 +399,48 @@ def time_ours(args, dist, out):
                                     "peak": peak, "unit": "TFLOP/s",
                                     "frac": flops / (ms / 1e3) / 1e12 / peak,
                                     "peak_kind": "FP32 FMA lanes x max SM clock"}}
+    # The codec with 16x16 and 32x32 blocks and the JAM matrices of §6.2, on
+    # the same images (the batch as one tall plane: 1024 is a multiple of the
+    # block sides, so no block straddles two images), reconstruction written.
+    if not args.no_jam and args.workload == "batch_1024x1024" and args.transform == "T1":
+        big = wl.storage[0].view(-1, wl.storage[0].shape[-1])
+        rec_big = torch.empty_like(big)
+        jsse = torch.zeros(1, dtype=torch.int64, device=dev)
+        jam = {}
+        for B in (16, 32):
+            T = jam_matrix(B)
+            for _ in range(2):
+                P.tdct_codec_error_jam(big, B, T, wl.desc["r"], jsse, recon=rec_big, stream=stream)
+            torch.cuda.synchronize()
+            j0 = torch.cuda.Event(enable_timing=True)
+            j1 = torch.cuda.Event(enable_timing=True)
+            j0.record(stream)
+            for _ in range(5):
+                P.tdct_codec_error_jam(big, B, T, wl.desc["r"], jsse, recon=rec_big, stream=stream)
+            j1.record(stream)
+            torch.cuda.synchronize()
+            ms = j0.elapsed_time(j1) / 5
+            gbs = 2 * big.numel() / (ms / 1e3) / 1e9
+            jam[f"B{B}"] = {"ms": ms, "r": wl.desc["r"], "pixels_per_s": big.numel() / (ms / 1e3),
+                            "hbm_gbs": gbs, "frac_of_measured_hbm": gbs / measured_peaks()[0]}
+        out["jam"] = jam
     plan.close()
     return wl
+
+
+def jam_matrix(B: int):
+    """T_(B) of §6.2 from T1 by the JAM rows: row 2i = [t_i, reverse(t_i)],
+    row 2i + 1 = [t_i, -reverse(t_i)] (t_i the rows of the half-size matrix)."""
+    from paper_1808_02950_gb300 import transforms as tr
+
+    cur = [list(r) for r in tr.T1]
+    while len(cur) < B:
+        nxt = []
+        for t in cur:
+            nxt.append(t + t[::-1])
+            nxt.append(t + [-v for v in t[::-1]])
+        cur = nxt
+    return cur
 
 
 def time_search(skip_cpu: bool):

@@ -213,6 +213,26 @@ int tdct_codec_error_batched_host(const tdct_plane* planes, int nplanes, const i
                                   size_t chunk_bytes, tdct_stream_t stream);
 
 /*
+ * tdct_codec_error_jam -- the codec of §6.1 with B x B blocks, B = 16 or 32,
+ * and the B-point transforms that §6.2 derives from T1 with the JAM
+ * recursion (T_(16) and T_(32) as printed there; Ĉ = S T with S from
+ * T T^T = diag(n), the 1/sqrt(2) of the recursion included in S).  Zonal
+ * retention keeps the first r positions of the B x B zig-zag scan (the 8x8
+ * rule extended: anti-diagonals, odd ones from (0, s) downwards, even ones
+ * from (s, 0) upwards); reconstruction, rounding and clamping as for 8x8
+ * blocks, bit-exact.
+ *   T, n      the B x B matrix (row-major int8) and its B squared row norms;
+ *             T must be T_(16) or T_(32) (TDCT_EUNSUPPORTED otherwise: the
+ *             kernels implement the JAM fast algorithm)
+ *   r         1..B^2
+ *   other arguments as tdct_codec_error; edge blocks are zero padded.
+ */
+int tdct_codec_error_jam(const void* d_img, int64_t pitch, int H, int W, int dtype, int B,
+                         const int8_t* T, const int32_t* n, int r, void* d_recon,
+                         int64_t recon_pitch, uint64_t* d_sse, double* d_psnr,
+                         tdct_stream_t stream);
+
+/*
  * tdct_ssim_batched -- mean structural similarity (MSSIM) of pairs of u8
  * planes, the third figure of merit of §6.1, with the index as defined by
  * Wang, Bovik, Sheikh and Simoncelli (2004), which §6.1 cites: an 11x11

@@ -34,7 +34,7 @@ N1 = (8, 18, 20, 18, 8, 18, 20, 18)
 EXPORTS = (
     "tdct_forward", "tdct_zonal_inverse", "tdct_codec_error", "tdct_codec_error_batched",
     "tdct_codec_error_batched_noalloc", "tdct_codec_error_batched_host", "tdct_ssim_batched",
-    "tdct_search",
+    "tdct_search", "tdct_codec_error_jam",
     "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_config",
     "tdct_plan_destroy",
     "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
@@ -82,6 +82,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_codec_error_batched_host.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.tdct_ssim_batched.argtypes = [vp, i32, vp, vp]
     L.tdct_search.argtypes = [i32, vp, i32, vp, i32, vp, vp, i32, i32, vp, vp, vp]
+    L.tdct_codec_error_jam.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp, i32, vp, i64, vp, vp,
+                                       vp]
     L.tdct_plan_create.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(ctypes.c_void_p)]
     L.tdct_plan_launch.argtypes = [vp, vp, vp, vp]
     L.tdct_plan_kernel_count.argtypes = [vp]
@@ -244,6 +246,17 @@ def tdct_ssim_batched(pairs, mssim, stream=None) -> None:
         arr[i] = TdctSsimPlane(_ptr(x), xp, _ptr(y), yp, H, W)
     _check(load().tdct_ssim_batched(ctypes.addressof(arr), len(pairs), _ptr(mssim),
                                     _stream(stream)))
+
+
+def tdct_codec_error_jam(img, B: int, T, r: int, sse, recon=None, psnr=None, stream=None) -> None:
+    """The codec with B x B blocks (16 or 32) and the JAM matrix T (B x B)."""
+    dt, H, W, pitch = _plane_info(img)
+    rp = _plane_info(recon)[3] if recon is not None else 0
+    flat = [int(v) for row in T for v in row]
+    tb = (ctypes.c_int8 * (B * B))(*flat)
+    nb = (ctypes.c_int32 * B)(*[sum(int(v) * int(v) for v in row) for row in T])
+    _check(load().tdct_codec_error_jam(_ptr(img), pitch, H, W, dt, int(B), tb, nb, int(r),
+                                       _ptr(recon), rp, _ptr(sse), _ptr(psnr), _stream(stream)))
 
 
 def tdct_search(N: int, alphabet, order, fixed=None, tie: str = "small", stream=None):

@@ -25,6 +25,7 @@
 #include "tdct_classes.h"
 #include "tdct_dct.h"
 #include "tdct_generic.cuh"
+#include "tdct_jam.h"
 #include "tdct_kernels.cuh"
 #include "tdct_search.h"
 #include "tdct_ssim.h"
@@ -1187,6 +1188,83 @@ int tdct_ssim_batched(const tdct_ssim_plane* planes, int nplanes, double* d_mssi
   const cudaError_t ef = cudaFreeAsync(scratch, s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_ssim_batched");
   if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  return TDCT_OK;
+}
+
+int tdct_codec_error_jam(const void* d_img, int64_t pitch, int H, int W, int dtype, int B,
+                         const int8_t* T, const int32_t* n, int r, void* d_recon,
+                         int64_t recon_pitch, uint64_t* d_sse, double* d_psnr,
+                         tdct_stream_t stream) {
+  if (B != 16 && B != 32) return fail(TDCT_EINVAL, "B = %d is neither 16 nor 32", B);
+  if (!T || !n) return fail(TDCT_EINVAL, "T and n must not be NULL");
+  if (r < 1 || r > B * B) return fail(TDCT_EINVAL, "r = %d outside 1..%d", r, B * B);
+  int rc = check_plane(d_img, pitch, H, W, dtype, "tdct_codec_error_jam");
+  if (rc) return rc;
+  if (d_recon && (rc = check_plane(d_recon, recon_pitch, H, W, dtype, "recon"))) return rc;
+  if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
+    return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
+  if (d_psnr && (reinterpret_cast<uintptr_t>(d_psnr) & 7))
+    return fail(TDCT_EINVAL, "d_psnr not 8-byte aligned");
+  for (int a = 0; a < B; ++a)
+    for (int c = 0; c < B; ++c) {
+      int64_t dot = 0;
+      for (int l = 0; l < B; ++l) dot += (int64_t)T[a * B + l] * T[c * B + l];
+      if (dot != (a == c ? (int64_t)n[a] : 0))
+        return fail(TDCT_ENOTORTHO, "(T T^T)[%d][%d] = %lld does not match diag(n)", a, c,
+                    (long long)dot);
+    }
+  // the JAM matrices from T1: row 2i = [t_i, reverse(t_i)], row 2i + 1 =
+  // [t_i, -reverse(t_i)] for the rows t_i of the half-size matrix
+  std::vector<int> cur(kT1, kT1 + 64);
+  for (int h = 8; h < B; h *= 2) {
+    std::vector<int> nxt(4 * h * h);
+    for (int i = 0; i < h; ++i)
+      for (int m = 0; m < h; ++m) {
+        const int t = cur[i * h + m];
+        nxt[(2 * i) * 2 * h + m] = t;
+        nxt[(2 * i) * 2 * h + 2 * h - 1 - m] = t;
+        nxt[(2 * i + 1) * 2 * h + m] = t;
+        nxt[(2 * i + 1) * 2 * h + 2 * h - 1 - m] = -t;
+      }
+    cur.swap(nxt);
+  }
+  for (int e = 0; e < B * B; ++e)
+    if (cur[e] != T[e])
+      return fail(TDCT_EUNSUPPORTED,
+                  "the %d-point kernels implement the JAM transform of T1 (§6.2) only", B);
+  JamParams jp;
+  std::memset(&jp, 0, sizeof jp);
+  int64_t L = 1;
+  for (int i = 0; i < B; ++i) L = L / gcd64(L, n[i]) * n[i];
+  for (int i = 0; i < B; ++i) jp.q[i] = (int32_t)(L / n[i]);
+  jp.L2 = L * L;
+  jp.limit = 256 * 2 * jp.L2;
+  jp.r = r;
+  const int64_t d = 2 * jp.L2;
+  int k = 32;
+  while (k < 62 && (((int64_t)1 << (k + 1)) + d - 1) / d < ((int64_t)1 << 32)) ++k;
+  const int64_t magic = (((int64_t)1 << k) + d - 1) / d;
+  const int64_t err = magic * d - ((int64_t)1 << k);
+  if (jp.limit >= ((int64_t)1 << 31) ||
+      (unsigned __int128)err * (unsigned __int128)jp.limit >= ((unsigned __int128)1 << k))
+    return fail(TDCT_EUNSUPPORTED, "no exact 32-bit division constant for L = %lld", (long long)L);
+  jp.magic = (uint32_t)magic;
+  jp.shift = k - 32;
+  const auto a16 = [](const void* p, int64_t pitch) {
+    return ((reinterpret_cast<uintptr_t>(p) | (uintptr_t)pitch) & 15) == 0;
+  };
+  jp.aligned = (a16(d_img, pitch) ? 1 : 0) | (d_recon && a16(d_recon, recon_pitch) ? 2 : 0);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
+  cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error_jam memset");
+  const PlaneDesc P = make_desc(d_img, pitch, H, W, dtype, 64, d_recon, recon_pitch, 0);
+  if ((e = launch_jam_codec(B, P, jp, sse, s)) != cudaSuccess)
+    return cuda_fail(e, "tdct_codec_error_jam launch");
+  if (d_psnr) {
+    psnr_kernel<<<1, 32, 0, s>>>(sse, nullptr, (int64_t)H * W, d_psnr, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "psnr launch");
+  }
   return TDCT_OK;
 }
 

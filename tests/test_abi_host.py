@@ -234,3 +234,24 @@ def test_search_rejects_before_any_cuda_call():
     big = (ctypes.c_int8 * 9)(*range(-4, 5))
     assert ok(16, big, 9, order, 2, None, None, 0, 0, T, ctypes.byref(c), None) \
         == _lib.TDCT_EUNSUPPORTED
+
+
+def test_jam_codec_rejects_before_any_cuda_call():
+    import numpy as np
+
+    from oracle import matrices as M
+
+    L = P.load()
+
+    def call(T, B=16, r=10, n=None):
+        Tb = (ctypes.c_int8 * (B * B))(*[int(v) for v in np.asarray(T).reshape(-1)])
+        nn = n if n is not None else [int(v) for v in np.einsum("ij,ij->i", T, T)]
+        nb = (ctypes.c_int32 * B)(*nn)
+        return L.tdct_codec_error_jam(FAKE, 64, 16, 64, 0, B, Tb, nb, r, None, 0, FAKE, None, None)
+
+    assert call(M.T16, r=0) == _lib.TDCT_EINVAL
+    assert call(M.T16, r=257) == _lib.TDCT_EINVAL
+    assert call(M.T1, B=8) == _lib.TDCT_EINVAL
+    swapped = M.T16[[1, 0] + list(range(2, 16))]           # orthogonal, not the JAM matrix
+    assert call(swapped) == _lib.TDCT_EUNSUPPORTED
+    assert call(M.T16, n=[16] * 16) == _lib.TDCT_ENOTORTHO

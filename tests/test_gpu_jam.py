@@ -1,0 +1,64 @@
+"""GPU parity of the 16x16 / 32x32 block codec with the JAM matrices of §6.2
+(tdct_codec_error_jam) against the CPU oracle, bit for bit: SSE, PSNR and
+reconstruction, u8 and int16 residual planes, ragged edges."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1808_02950_gb300 as P
+from oracle import codec as oc
+from oracle import matrices as M
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def run(host, B, T, r):
+    view = torch.from_numpy(host).to(DEV)
+    recon = torch.full_like(view, 7)
+    sse = torch.zeros(1, dtype=torch.int64, device=DEV)
+    psnr = torch.zeros(1, dtype=torch.float64, device=DEV)
+    P.tdct_codec_error_jam(view, B, T.tolist(), r, sse, recon=recon, psnr=psnr)
+    torch.cuda.synchronize()
+    return int(sse.item()), recon.cpu().numpy(), float(psnr.item())
+
+
+@pytest.mark.parametrize("B,T", [(16, M.T16), (32, M.T32)])
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+@pytest.mark.parametrize("H,W", [(16, 16), (40, 70), (33, 97), (64, 128), (7, 5)])
+def test_jam_codec_matches_oracle(B, T, dtype, H, W):
+    rng = np.random.default_rng(B * 1000 + H * 10 + W + (dtype == np.int16))
+    if dtype == np.uint8:
+        host = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    else:
+        host = rng.integers(-255, 256, (H, W)).astype(np.int16)
+    for r in (1, 3, 10, 50, 136, B * B // 2, B * B):
+        sse, rec, psnr = run(host, B, T, r)
+        want_sse, want_rec = oc.codec_plane_b(host, T, B, r)
+        assert np.array_equal(rec, want_rec), f"B={B} r={r}"
+        assert sse == want_sse
+        if want_sse:
+            assert psnr == pytest.approx(oc.psnr(want_sse, H * W), rel=1e-12)
+
+
+@pytest.mark.parametrize("B,T", [(16, M.T16), (32, M.T32)])
+def test_jam_codec_smooth_image_and_extremes(B, T):
+    """A synthetic AR(1) image (the paper's image statistics) and extreme
+    blocks (constants, checkerboards, sign patterns of the basis)."""
+    from paper_1808_02950_gb300 import synth
+
+    img = synth.ar1_images(1, 128, 256, 0.95, 11, "cpu")[0].numpy()
+    for r in (3, 21, 100):
+        sse, rec, _ = run(np.ascontiguousarray(img), B, T, r)
+        want_sse, want_rec = oc.codec_plane_b(np.ascontiguousarray(img), T, B, r)
+        assert sse == want_sse and np.array_equal(rec, want_rec)
+    blocks = [np.zeros((B, B)), np.full((B, B), 255),
+              (np.indices((B, B)).sum(0) % 2) * 255]
+    for i in (0, 1, B // 2 - 1, B - 1):
+        s = np.sign(np.outer(T[i], T[(3 * i + 1) % B]))
+        blocks.append(np.where(s > 0, 255, 0))
+    ext = np.ascontiguousarray(np.concatenate([b.astype(np.uint8) for b in blocks], axis=1))
+    for r in (1, 5, B * B):
+        sse, rec, _ = run(ext, B, T, r)
+        want_sse, want_rec = oc.codec_plane_b(ext, T, B, r)
+        assert sse == want_sse and np.array_equal(rec, want_rec)
