@@ -401,6 +401,25 @@ struct RowsInSmem {
   }
 };
 
+// SSE per row of 8 samples.  1: per-byte absolute differences |x - x'|
+// (vabsdiff4), squared and summed by one byte dot product per 4 samples;
+// 0: sum x^2 + sum x'^2 - 2 sum x x' from three byte dot products per 4
+// samples (sum x^2 formed once per block).
+#ifndef TDCT_SSE_ABSDIFF
+#define TDCT_SSE_ABSDIFF 1
+#endif
+
+__device__ __forceinline__ uint32_t row_sse_terms(uint2 xk, uint2 y, uint32_t acc) {
+#if TDCT_SSE_ABSDIFF
+  const uint32_t d0 = __vabsdiffu4(xk.x, y.x), d1 = __vabsdiffu4(xk.y, y.y);
+  return __dp4a(d0, d0, __dp4a(d1, d1, acc));
+#else
+  acc = __dp4a(y.x, y.x, acc);
+  acc = __dp4a(y.y, y.y, acc);
+  return acc - 2u * __dp4a(xk.x, y.x, __dp4a(xk.y, y.y, 0u));
+#endif
+}
+
 // 1: accumulate each row's SSE terms into one running sum (a dependency
 // chain across rows); 0: form each row's terms independently.
 #ifndef TDCT_SSE_CHAIN
@@ -442,10 +461,8 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8(const uint32_t w[64], XS
       y.y &= (uint32_t)(m >> 32);
     }
     const uint2 xk = x.row(k);
-#if TDCT_SSE_CHAIN
-    acc = __dp4a(y.x, y.x, acc);
-    acc = __dp4a(y.y, y.y, acc);
-    acc -= 2u * __dp4a(xk.x, y.x, __dp4a(xk.y, y.y, 0u));
+#if TDCT_SSE_CHAIN || TDCT_SSE_ABSDIFF
+    acc = row_sse_terms(xk, y, acc);
 #else
     // per-row partials are independent; only the final add joins them
     const uint32_t yy = __dp4a(y.x, y.x, __dp4a(y.y, y.y, 0u));
@@ -529,9 +546,7 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8_rows(const uint32_t w[64
       y.y &= (uint32_t)(m >> 32);
     }
     const uint2 xk = x.row(k);
-    acc = __dp4a(y.x, y.x, acc);
-    acc = __dp4a(y.y, y.y, acc);
-    acc -= 2u * __dp4a(xk.x, y.x, __dp4a(xk.y, y.y, 0u));
+    acc = row_sse_terms(xk, y, acc);
     if (store && full) out_row0[(int64_t)k * (out_pitch >> 3)] = y;
     if (store && !full && k < valid_rows) {
       uint8_t* row = reinterpret_cast<uint8_t*>(out_row0) + (int64_t)k * out_pitch;
@@ -578,6 +593,7 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
   const bool full0 = FULL || (valid_rows == 8 && vc0 == 8);
   const bool full1 = FULL || (has1 && valid_rows == 8 && vc1 == 8);
   uint32_t sse = 0;
+#if !TDCT_SSE_ABSDIFF
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const uint2 a = xa.row(k), b = xb.row(k);
@@ -586,6 +602,7 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
     sse = __dp4a(b.x, b.x, sse);
     sse = __dp4a(b.y, b.y, sse);
   }
+#endif
   // packed forward.  The first pass forms, for each of the 8 rows (or
   // columns), only the outputs inside the kept columns (rows); the second
   // only the kept positions.  Rows first when the kept set is no wider than

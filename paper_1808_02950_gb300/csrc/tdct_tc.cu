@@ -292,10 +292,12 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, false>())
       for (int k = 0; k < 8; ++k) {
         xa[k] = make_uint2(rw[k].x, rw[k].y);
         xb[k] = make_uint2(rw[k].z, rw[k].w);
+#if !TDCT_SSE_ABSDIFF  // the epilogue's terms then need sum x^2
         sse = __dp4a(xa[k].x, xa[k].x, sse);
         sse = __dp4a(xa[k].y, xa[k].y, sse);
         sse = __dp4a(xb[k].x, xb[k].x, sse);
         sse = __dp4a(xb[k].y, xb[k].y, sse);
+#endif
       }
       const bool store = P.recon != nullptr;
       const int64_t rp = P.recon_pitch;
@@ -546,10 +548,12 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, true>())
           const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + k * P.pitch));
           xa[k] = make_uint2(v.x, v.y);
           xb[k] = make_uint2(v.z, v.w);
+#if !TDCT_SSE_ABSDIFF  // the epilogue's terms then need sum x^2
           sse = __dp4a(xa[k].x, xa[k].x, sse);
           sse = __dp4a(xa[k].y, xa[k].y, sse);
           sse = __dp4a(xb[k].x, xb[k].x, sse);
           sse = __dp4a(xb[k].y, xb[k].y, sse);
+#endif
         }
         const bool store = P.recon != nullptr;
         const int64_t rp = P.recon_pitch;
