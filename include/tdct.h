@@ -272,7 +272,7 @@ int tdct_ssim_batched(const tdct_ssim_plane* planes, int nplanes, double* d_mssi
  * tie; `tie` 0 keeps the smaller-norm vector, 1 the larger, then the first
  * in the enumeration.
  *   N           blocklength, 2..16
- *   alphabet    np distinct values in [-127, 127], 2 <= np <= 9,
+ *   alphabet    np distinct values in [-16, 16], 2 <= np <= 9,
  *               np^N <= 2^31
  *   order       n_order distinct rows (0-based), searched in this order
  *   fixed_rows  n_fixed distinct preset rows (0-based; not in `order`),

@@ -1282,8 +1282,11 @@ int tdct_search(int N, const int8_t* alphabet, int np, const int32_t* order, int
   std::memset(&sp, 0, sizeof sp);
   std::vector<int> vals(alphabet, alphabet + np);
   std::sort(vals.begin(), vals.end());
+  int maxabs = 0;
   for (int a = 0; a < np; ++a) {
-    if (vals[a] < -127) return fail(TDCT_EINVAL, "alphabet value %d below -127", vals[a]);
+    if (vals[a] < -kSearchMaxAbs || vals[a] > kSearchMaxAbs)
+      return fail(TDCT_EINVAL, "alphabet value %d outside [-16, 16]", vals[a]);
+    maxabs = std::max(maxabs, std::abs(vals[a]));
     if (a > 0 && vals[a] == vals[a - 1]) return fail(TDCT_EINVAL, "alphabet repeats %d", vals[a]);
     sp.alphabet[a] = vals[a];
   }
@@ -1306,6 +1309,7 @@ int tdct_search(int N, const int8_t* alphabet, int np, const int32_t* order, int
   }
   sp.np = np;
   sp.N = N;
+  sp.max_n2 = N * maxabs * maxabs;
   sp.total = (uint32_t)total;
   sp.n_fixed = n_fixed;
   sp.tie_large = tie;

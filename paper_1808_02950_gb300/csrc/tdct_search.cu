@@ -50,47 +50,118 @@ __device__ __forceinline__ void decode(uint32_t idx, int N, const SearchParams& 
   }
 }
 
+// Digits per table group: NP^G entries per group stay small.
+template <int NP>
+__host__ __device__ constexpr int group_digits() {
+  return NP <= 7 ? 4 : 3;
+}
+template <int NP>
+__host__ __device__ constexpr int group_entries() {
+  int e = 1;
+  for (int t = 0; t < group_digits<NP>(); ++t) e *= NP;
+  return e;
+}
+
+// Shared-memory tables of one row's pass, per group g of G digits and per
+// digit combination c of that group: the FP64 partial dot product with the
+// exact DCT row, the partial squared norm and the partial dot product with
+// `against` (the row chosen last, or a preset).  A candidate is the sum of
+// its groups' entries.
+template <int NP>
+__device__ __forceinline__ void build_tables(const SearchParams& sp, const int8_t* against_rev,
+                                             double* dtab, int* ntab, int* otab, int groups) {
+  constexpr int G = group_digits<NP>(), E = group_entries<NP>();
+  for (int e = threadIdx.x; e < groups * E; e += blockDim.x) {
+    const int g = e / E;
+    int c = e - g * E;
+    double d = 0.0;
+    int n2 = 0, o = 0;
+    for (int t = 0; t < G; ++t) {
+      const int k = g * G + t, dg = c % NP;
+      c /= NP;
+      if (k < sp.N) {
+        const int v = sp.alphabet[dg];
+        d = fma(sp.crow_rev[k], (double)v, d);
+        n2 += v * v;
+        o += v * (against_rev ? against_rev[k] : 0);
+      }
+    }
+    dtab[e] = d;
+    ntab[e] = n2;
+    otab[e] = o;
+  }
+}
+
+// Allowed-set initialisation and presets: cosv[i] = 0 for candidates that
+// are nonzero and orthogonal to the preset (or to nothing), -inf otherwise.
+template <int NP>
+__global__ void __launch_bounds__(256) search_filter(SearchParams sp, double* __restrict__ cosv,
+                                                     int preset, int init) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int E = group_entries<NP>(), G = group_digits<NP>();
+  const int groups = (sp.N + G - 1) / G;
+  double* dtab = reinterpret_cast<double*>(smem_raw) + (sp.max_n2 + 1);
+  int* ntab = reinterpret_cast<int*>(dtab + groups * E);
+  int* otab = ntab + groups * E;
+  __shared__ int8_t rev[kSearchMaxN];
+  if (threadIdx.x < kSearchMaxN)
+    rev[threadIdx.x] = (preset >= 0 && threadIdx.x < sp.N) ? sp.fixed[preset][sp.N - 1 - threadIdx.x] : 0;
+  __syncthreads();
+  build_tables<NP>(sp, rev, dtab, ntab, otab, groups);
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
+       i += gridDim.x * blockDim.x) {
+    if (!init && cosv[i] == -INFINITY) continue;
+    uint32_t idx = i;
+    int n2 = 0, o = 0;
+    for (int g = 0; g < groups; ++g) {
+      const uint32_t q = idx / E, c = idx - q * E;
+      idx = q;
+      n2 += ntab[g * E + c];
+      o += otab[g * E + c];
+    }
+    const bool ok = n2 > 0 && o == 0;
+    if (init || !ok) cosv[i] = ok ? 0.0 : -INFINITY;
+  }
+}
+
 template <int NP>
 __global__ void __launch_bounds__(256) search_max(SearchParams sp, SearchState* __restrict__ st,
                                                   double* __restrict__ cosv, int first) {
   if (st->dead) return;
-  __shared__ int8_t against[kSearchMaxN][kSearchMaxN];  // reversed rows to test against
-  __shared__ int n_against;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int E = group_entries<NP>(), G = group_digits<NP>();
+  const int groups = (sp.N + G - 1) / G;
+  double* inv_norm = reinterpret_cast<double*>(smem_raw);  // 1 / sqrt(n2), n2 = 0..max_n2
+  double* dtab = inv_norm + (sp.max_n2 + 1);
+  int* ntab = reinterpret_cast<int*>(dtab + groups * E);
+  int* otab = ntab + groups * E;
+  __shared__ int8_t rev[kSearchMaxN];
   __shared__ unsigned long long warp_best[8];
-  if (threadIdx.x == 0) n_against = first ? sp.n_fixed : 1;
-  for (int e = threadIdx.x; e < kSearchMaxN * kSearchMaxN; e += blockDim.x) {
-    const int r = e / kSearchMaxN, k = e % kSearchMaxN;
-    int8_t val = 0;
-    if (k < sp.N) {
-      if (first) val = r < sp.n_fixed ? sp.fixed[r][sp.N - 1 - k] : 0;
-      else val = r == 0 ? st->last_row[sp.N - 1 - k] : 0;
-    }
-    against[r][k] = val;
-  }
+  if (threadIdx.x < kSearchMaxN)
+    rev[threadIdx.x] = (!first && threadIdx.x < sp.N) ? st->last_row[sp.N - 1 - threadIdx.x] : 0;
+  for (int q = threadIdx.x; q <= sp.max_n2; q += blockDim.x)
+    inv_norm[q] = q > 0 ? 1.0 / sqrt((double)q) : 0.0;
   __syncthreads();
-  const int nag = n_against;
+  build_tables<NP>(sp, first ? nullptr : rev, dtab, ntab, otab, groups);
+  __syncthreads();
   unsigned long long best = 0ull;  // below every key of a finite value
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
        i += gridDim.x * blockDim.x) {
-    if (!first && cosv[i] == -INFINITY) continue;
-    int v[kSearchMaxN];
-    decode<NP>(i, sp.N, sp, v);
-    int n2 = 0;
-#pragma unroll
-    for (int k = 0; k < kSearchMaxN; ++k) n2 += v[k] * v[k];
-    bool ok = n2 > 0;
-    for (int r = 0; r < nag && ok; ++r) {
-      int dot = 0;
-#pragma unroll
-      for (int k = 0; k < kSearchMaxN; ++k) dot += v[k] * against[r][k];
-      ok = dot == 0;
+    if (cosv[i] == -INFINITY) continue;
+    uint32_t idx = i;
+    int n2 = 0, o = 0;
+    double dot = 0.0;
+    for (int g = 0; g < groups; ++g) {
+      const uint32_t q = idx / E, c = idx - q * E;
+      idx = q;
+      n2 += ntab[g * E + c];
+      o += otab[g * E + c];
+      dot += dtab[g * E + c];
     }
     double c = -INFINITY;
-    if (ok) {
-      double dot = 0.0;
-#pragma unroll
-      for (int k = 0; k < kSearchMaxN; ++k) dot = fma(sp.crow_rev[k], (double)v[k], dot);
-      c = dot / sqrt((double)n2);
+    if (o == 0) {  // nonzero and orthogonal to the presets: filtered before
+      c = dot * inv_norm[n2];
       const unsigned long long key = order_key(c);
       best = key > best ? key : best;
     }
@@ -155,9 +226,36 @@ __global__ void search_commit(SearchParams sp, SearchState* __restrict__ st, int
 }
 
 template <int NP>
+size_t table_bytes(const SearchParams& sp) {
+  constexpr int G = group_digits<NP>();
+  return sizeof(double) * (size_t)(sp.max_n2 + 1) +
+         (size_t)((sp.N + G - 1) / G) * group_entries<NP>() * (sizeof(double) + 2 * sizeof(int));
+}
+
+template <int NP>
 cudaError_t enqueue_row(const SearchParams& sp, SearchState* st, double* cosv, int first,
                         int slot, int grid, cudaStream_t s) {
-  search_max<NP><<<grid, 256, 0, s>>>(sp, st, cosv, first);
+  const size_t smem = table_bytes<NP>(sp);
+  // the opt-in shared-memory limit is raised once per instantiation, to the
+  // largest table any accepted (alphabet, N) needs
+  static int limit_set = 0;
+  if (!limit_set) {
+    constexpr int kMaxSmem = 140 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(search_max<NP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(search_filter<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kMaxSmem);
+    if (e != cudaSuccess) return e;
+    limit_set = 1;
+  }
+  if (smem > 140 * 1024) return cudaErrorInvalidValue;
+  if (first) {
+    // allowed set: nonzero candidates orthogonal to every preset
+    search_filter<NP><<<grid, 256, smem, s>>>(sp, cosv, -1, 1);
+    for (int f = 0; f < sp.n_fixed; ++f) search_filter<NP><<<grid, 256, smem, s>>>(sp, cosv, f, 0);
+  }
+  search_max<NP><<<grid, 256, smem, s>>>(sp, st, cosv, first);
   search_pick<NP><<<grid, 256, 0, s>>>(sp, st, cosv);
   search_commit<NP><<<1, 1, 0, s>>>(sp, st, slot);
   return cudaGetLastError();

@@ -8,6 +8,7 @@ namespace tdct {
 
 constexpr int kSearchMaxN = 16;
 constexpr double kSearchTieTol = 1e-12;
+constexpr int kSearchMaxAbs = 16;  // alphabet values lie in [-16, 16]
 
 struct SearchParams {
   double crow_rev[kSearchMaxN];         // exact DCT row, coordinates reversed, zero past N
@@ -17,6 +18,7 @@ struct SearchParams {
   uint32_t total;                       // np^N candidates (zero vector included)
   int32_t n_fixed;
   int32_t tie_large;                    // 0: smaller norm first, 1: larger
+  int32_t max_n2;                       // N * max(v^2): largest squared norm
   int8_t fixed[kSearchMaxN][kSearchMaxN];  // preset rows (coordinate order)
 };
 

@@ -231,6 +231,8 @@ def test_search_rejects_before_any_cuda_call():
     bad = (ctypes.c_int32 * 2)(0, 0)
     assert ok(8, alph, 3, bad, 2, None, None, 0, 0, T, ctypes.byref(c), None) == _lib.TDCT_EINVAL
     assert ok(8, alph, 3, order, 2, None, None, 0, 2, T, ctypes.byref(c), None) == _lib.TDCT_EINVAL
+    wide = (ctypes.c_int8 * 3)(0, 17, -1)
+    assert ok(8, wide, 3, order, 2, None, None, 0, 0, T, ctypes.byref(c), None) == _lib.TDCT_EINVAL
     big = (ctypes.c_int8 * 9)(*range(-4, 5))
     assert ok(16, big, 9, order, 2, None, None, 0, 0, T, ctypes.byref(c), None) \
         == _lib.TDCT_EUNSUPPORTED
