@@ -48,6 +48,33 @@ struct HSums {
   float C;   // sum g x y
 };
 
+// One ring step: the new row's horizontal sums go to slot K; when 11 rows
+// are in, the vertical sums over slots K+1 .. K (oldest first).  One
+// instantiation per slot keeps the ring in registers; the row loop itself
+// stays rolled (its body appears once), which keeps the code within the
+// instruction cache.
+template <int K>
+__device__ __forceinline__ void ring_step(HSums (&r0)[kSsimWin], HSums (&r1)[kSsimWin],
+                                          const HSums& n0, const HSums& n1, bool ready,
+                                          const SsimParams& sp, HSums& v0, HSums& v1) {
+  r0[K] = n0;
+  r1[K] = n1;
+  if (!ready) return;
+  v0 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
+  v1 = v0;
+#pragma unroll
+  for (int i = 0; i < kSsimWin; ++i) {
+    const int sl = (K + 1 + i) % kSsimWin;
+    const float2 g = make_float2(sp.g[i], sp.g[i]);
+    v0.A = __ffma2_rn(g, r0[sl].A, v0.A);
+    v0.B = __ffma2_rn(g, r0[sl].B, v0.B);
+    v0.C = fmaf(sp.g[i], r0[sl].C, v0.C);
+    v1.A = __ffma2_rn(g, r1[sl].A, v1.A);
+    v1.B = __ffma2_rn(g, r1[sl].B, v1.B);
+    v1.C = fmaf(sp.g[i], r1[sl].C, v1.C);
+  }
+}
+
 __global__ void __launch_bounds__(128, 2)
     ssim_kernel(const SsimDesc* __restrict__ descs, int n, int64_t total_units,
                 const SsimParams sp, double* __restrict__ out) {
@@ -101,77 +128,73 @@ __global__ void __launch_bounds__(128, 2)
       }
     };
     load_row(o0);
-    for (int rb = o0; rb < r_end; rb += kSsimWin) {
+    int kslot = 0;  // ring slot of the current row: (row - o0) mod 11
+#pragma unroll 1
+    for (int row = o0; row < r_end; ++row) {
+      float2* buf = rowbuf[wid][row & 1];
+      const float2 a0 = centred_pair(nx0, ny0), a1 = centred_pair(nx1, ny1);
+      float2 ha0, ha1;
+      if (lane < (kSsimWin - 1) / 2) {
+        ha0 = centred_pair(nhx0, nhy0);
+        ha1 = centred_pair(nhx1, nhy1);
+      }
+      if (row + 1 < r_end) load_row(row + 1);  // one row ahead
+      *reinterpret_cast<float4*>(buf + cl) = make_float4(a0.x, a0.y, a1.x, a1.y);
+      if (lane < (kSsimWin - 1) / 2)
+        *reinterpret_cast<float4*>(buf + kSsimStrip + cl) = make_float4(ha0.x, ha0.y, ha1.x, ha1.y);
+      __syncwarp();
+      // the lane's 12 input columns (cl .. cl + 11), their squares and products
+      float2 a[kSsimWin + 1], q[kSsimWin + 1];
+      float c[kSsimWin + 1];
 #pragma unroll
-      for (int k = 0; k < kSsimWin; ++k) {
-        const int row = rb + k;
-        if (row >= r_end) break;  // uniform across the warp
-        float2* buf = rowbuf[wid][row & 1];
-        const float2 a0 = centred_pair(nx0, ny0), a1 = centred_pair(nx1, ny1);
-        float2 ha0, ha1;
-        if (lane < (kSsimWin - 1) / 2) {
-          ha0 = centred_pair(nhx0, nhy0);
-          ha1 = centred_pair(nhx1, nhy1);
-        }
-        if (row + 1 < r_end) load_row(row + 1);  // one row ahead
-        *reinterpret_cast<float4*>(buf + cl) = make_float4(a0.x, a0.y, a1.x, a1.y);
-        if (lane < (kSsimWin - 1) / 2)
-          *reinterpret_cast<float4*>(buf + kSsimStrip + cl) = make_float4(ha0.x, ha0.y, ha1.x, ha1.y);
-        __syncwarp();
-        // the lane's 12 input columns (cl .. cl + 11), their squares and products
-        float2 a[kSsimWin + 1], q[kSsimWin + 1];
-        float c[kSsimWin + 1];
+      for (int t = 0; t < (kSsimWin + 1) / 2; ++t) {
+        const float4 v = *reinterpret_cast<const float4*>(buf + cl + 2 * t);
+        a[2 * t] = make_float2(v.x, v.y);
+        a[2 * t + 1] = make_float2(v.z, v.w);
+      }
 #pragma unroll
-        for (int t = 0; t < (kSsimWin + 1) / 2; ++t) {
-          const float4 v = *reinterpret_cast<const float4*>(buf + cl + 2 * t);
-          a[2 * t] = make_float2(v.x, v.y);
-          a[2 * t + 1] = make_float2(v.z, v.w);
-        }
+      for (int t = 0; t <= kSsimWin; ++t) {
+        q[t] = __fmul2_rn(a[t], a[t]);
+        c[t] = a[t].x * a[t].y;
+      }
+      HSums n0 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
+      HSums n1 = n0;
 #pragma unroll
-        for (int t = 0; t <= kSsimWin; ++t) {
-          q[t] = __fmul2_rn(a[t], a[t]);
-          c[t] = a[t].x * a[t].y;
-        }
-        HSums n0 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
-        HSums n1 = n0;
-#pragma unroll
-        for (int j = 0; j < kSsimWin; ++j) {
-          const float2 g = make_float2(sp.g[j], sp.g[j]);
-          n0.A = __ffma2_rn(g, a[j], n0.A);
-          n0.B = __ffma2_rn(g, q[j], n0.B);
-          n0.C = fmaf(sp.g[j], c[j], n0.C);
-          n1.A = __ffma2_rn(g, a[j + 1], n1.A);
-          n1.B = __ffma2_rn(g, q[j + 1], n1.B);
-          n1.C = fmaf(sp.g[j], c[j + 1], n1.C);
-        }
-        r0[k] = n0;
-        r1[k] = n1;
-        if (row - o0 >= kSsimWin - 1) {
-          // vertical over the last 11 rows, oldest first: slots k+1 .. k (mod 11)
-          HSums v0 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), 0.f};
-          HSums v1 = v0;
-#pragma unroll
-          for (int i = 0; i < kSsimWin; ++i) {
-            const int sl = (k + 1 + i) % kSsimWin;
-            const float2 g = make_float2(sp.g[i], sp.g[i]);
-            v0.A = __ffma2_rn(g, r0[sl].A, v0.A);
-            v0.B = __ffma2_rn(g, r0[sl].B, v0.B);
-            v0.C = fmaf(sp.g[i], r0[sl].C, v0.C);
-            v1.A = __ffma2_rn(g, r1[sl].A, v1.A);
-            v1.B = __ffma2_rn(g, r1[sl].B, v1.B);
-            v1.C = fmaf(sp.g[i], r1[sl].C, v1.C);
-          }
-          auto ssim_of = [&](const HSums& v) {
-            const float mx = v.A.x + 128.0f, my = v.A.y + 128.0f;
-            const float sxx = v.B.x - v.A.x * v.A.x, syy = v.B.y - v.A.y * v.A.y;
-            const float sxy = v.C - v.A.x * v.A.y;
-            const float num = (2.0f * mx * my + sp.C1) * (2.0f * sxy + sp.C2);
-            const float den = (mx * mx + my * my + sp.C1) * (sxx + syy + sp.C2);
-            return __fdividef(num, den);
-          };
-          if (ok0) lane_sum += ssim_of(v0);
-          if (ok1) lane_sum += ssim_of(v1);
-        }
+      for (int j = 0; j < kSsimWin; ++j) {
+        const float2 g = make_float2(sp.g[j], sp.g[j]);
+        n0.A = __ffma2_rn(g, a[j], n0.A);
+        n0.B = __ffma2_rn(g, q[j], n0.B);
+        n0.C = fmaf(sp.g[j], c[j], n0.C);
+        n1.A = __ffma2_rn(g, a[j + 1], n1.A);
+        n1.B = __ffma2_rn(g, q[j + 1], n1.B);
+        n1.C = fmaf(sp.g[j], c[j + 1], n1.C);
+      }
+      const bool ready = row - o0 >= kSsimWin - 1;
+      HSums v0, v1;
+      switch (kslot) {
+#define TDCT_SSIM_SLOT(K) \
+  case K:                 \
+    ring_step<K>(r0, r1, n0, n1, ready, sp, v0, v1); \
+    break;
+        TDCT_SSIM_SLOT(0) TDCT_SSIM_SLOT(1) TDCT_SSIM_SLOT(2) TDCT_SSIM_SLOT(3)
+        TDCT_SSIM_SLOT(4) TDCT_SSIM_SLOT(5) TDCT_SSIM_SLOT(6) TDCT_SSIM_SLOT(7)
+        TDCT_SSIM_SLOT(8) TDCT_SSIM_SLOT(9) TDCT_SSIM_SLOT(10)
+#undef TDCT_SSIM_SLOT
+        default:
+          break;
+      }
+      kslot = kslot == kSsimWin - 1 ? 0 : kslot + 1;
+      if (ready) {
+        auto ssim_of = [&](const HSums& v) {
+          const float mx = v.A.x + 128.0f, my = v.A.y + 128.0f;
+          const float sxx = v.B.x - v.A.x * v.A.x, syy = v.B.y - v.A.y * v.A.y;
+          const float sxy = v.C - v.A.x * v.A.y;
+          const float num = (2.0f * mx * my + sp.C1) * (2.0f * sxy + sp.C2);
+          const float den = (mx * mx + my * my + sp.C1) * (sxx + syy + sp.C2);
+          return __fdividef(num, den);
+        };
+        if (ok0) lane_sum += ssim_of(v0);
+        if (ok1) lane_sum += ssim_of(v1);
       }
     }
     acc += (double)lane_sum;
