@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "tdct_jam.h"
 #include "tdct_kernels.cuh"
@@ -114,18 +115,28 @@ struct RowRaw {
   }
 };
 
+// The column inverse V' = T^T (2 q o Z) of a column is exact in 32 bits
+// when |V'| < 2^31: at B = 16, |Z| <= 146880 and |V'| <= 16 * 2 * 90 * |Z|
+// < 4.3e8 for both sample types; at B = 32, u8 gives |Z| <= 293760 and
+// |V'| <= 32 * 2 * 90 * |Z| < 1.7e9, int16 residuals do not fit.  There the
+// stage and both transposes run in 32 bits, elsewhere in 64.
+template <int B, int DT>
+using StageA = std::conditional_t<(B == 16 || DT == 0), uint32_t, long long>;
+
 template <int B, int DT>
 __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const JamParams jp,
                                                         unsigned long long* __restrict__ sse_out) {
   constexpr int BPW = 32 / B;  // blocks per warp
   constexpr int SB = DT == 0 ? 1 : 2;
-  __shared__ long long tile[4][BPW][B][B + 1];
+  using VA = StageA<B, DT>;
+  using TileT = std::conditional_t<std::is_same_v<VA, uint32_t>, int32_t, long long>;
+  __shared__ TileT tile[4][BPW][B][B + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int bsub = lane / B, k = lane % B;
   const int64_t nbx = (P.W + B - 1) / B, nby = (P.H + B - 1) / B, nb = nbx * nby;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  long long (*tl)[B + 1] = tile[wid][bsub];
+  TileT (*tl)[B + 1] = tile[wid][bsub];
   const int hk = kept_height(B, jp.r, k);  // the lane's column in the column stage
   unsigned long long acc = 0;
   for (int64_t base = warp * BPW; base < nb; base += nwarps * BPW) {
@@ -160,7 +171,7 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
       for (int l = 0; l < B; ++l) x[l] = (uint32_t)raw.at(l);
       jam_fwd<B, uint32_t>(x, t);
 #pragma unroll
-      for (int j = 0; j < B; ++j) tl[k][j] = (long long)(int32_t)t[j];
+      for (int j = 0; j < B; ++j) tl[k][j] = (TileT)(int32_t)t[j];
     }
     __syncwarp();
     // column c = k: Z[i][c], zonal mask with 2 q_i, inverse along the column
@@ -169,20 +180,21 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
 #pragma unroll
       for (int i = 0; i < B; ++i) col[i] = (uint32_t)tl[i][k];
       jam_fwd<B, uint32_t>(col, z);
-      long long w[B], u[B];
+      VA w[B], u[B];
 #pragma unroll
-      for (int i = 0; i < B; ++i) w[i] = i < hk ? (long long)(int32_t)z[i] * (2 * jp.q[i]) : 0ll;
-      jam_inv<B, long long>(w, u);
+      for (int i = 0; i < B; ++i)
+        w[i] = i < hk ? (VA)((long long)(int32_t)z[i] * (2 * jp.q[i])) : (VA)0;
+      jam_inv<B, VA>(w, u);
       __syncwarp();
 #pragma unroll
-      for (int i = 0; i < B; ++i) tl[i][k] = u[i];
+      for (int i = 0; i < B; ++i) tl[i][k] = (TileT)u[i];
     }
     __syncwarp();
     // row k: 2N[k][l] = sum_j q_j V'[k][j] T[j][l]; round, clamp, error, store
     {
       long long v[B], n2[B];
 #pragma unroll
-      for (int j = 0; j < B; ++j) v[j] = tl[k][j] * jp.q[j];
+      for (int j = 0; j < B; ++j) v[j] = (long long)tl[k][j] * jp.q[j];
       jam_inv<B, long long>(v, n2);
       RowRaw<B, DT> out;
       uint32_t* ou = reinterpret_cast<uint32_t*>(out.w);
