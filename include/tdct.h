@@ -283,7 +283,7 @@ int tdct_ssim_batched(const tdct_ssim_plane* planes, int nplanes, double* d_mssi
  *   complete    host output: 1, or 0 when some row had no orthogonal
  *               candidate left (the rows before it are in T_out)
  * Synchronous: the call waits for its work on `stream`.  Device scratch of
- * 8 np^N bytes comes from the stream-ordered pool.
+ * np^N bytes (one per candidate) comes from the stream-ordered pool.
  * Errors: TDCT_EINVAL (arguments), TDCT_EUNSUPPORTED (np^N > 2^31),
  * TDCT_ENOMEM, TDCT_ECUDA.
  */

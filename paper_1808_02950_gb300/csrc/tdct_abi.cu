@@ -1315,11 +1315,11 @@ int tdct_search(int N, const int8_t* alphabet, int np, const int32_t* order, int
   sp.tie_large = tie;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void* block = nullptr;
-  const size_t bytes_cos = round_up(sizeof(double) * (size_t)total, 256);
-  cudaError_t e = cudaMallocAsync(&block, bytes_cos + sizeof(SearchState), s);
+  const size_t bytes_mask = round_up((size_t)total, 256);
+  cudaError_t e = cudaMallocAsync(&block, bytes_mask + sizeof(SearchState), s);
   if (e != cudaSuccess) return fail(TDCT_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
-  double* cosv = static_cast<double*>(block);
-  SearchState* st = reinterpret_cast<SearchState*>(static_cast<char*>(block) + bytes_cos);
+  uint8_t* allowed = static_cast<uint8_t*>(block);
+  SearchState* st = reinterpret_cast<SearchState*>(static_cast<char*>(block) + bytes_mask);
   SearchState init;
   std::memset(&init, 0, sizeof init);
   init.pick_key = ~0ull;
@@ -1332,7 +1332,7 @@ int tdct_search(int N, const int8_t* alphabet, int np, const int32_t* order, int
       const double ck = k == 0 ? std::sqrt(1.0 / N) : std::sqrt(2.0 / N);
       sp.crow_rev[N - 1 - j] = ck * std::cos(M_PI * (2.0 * j + 1.0) * k / (2.0 * N));
     }
-    e = enqueue_search_row(sp, st, cosv, i == 0, i, s);
+    e = enqueue_search_row(sp, st, allowed, i == 0, i, s);
   }
   SearchState out;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&out, st, sizeof out, cudaMemcpyDeviceToHost, s);

@@ -10,14 +10,26 @@
 // with values within 1e-12 of the maximum counted as ties, decided by the
 // norm (smaller or larger first) and then by the enumeration index.
 //
-// Per row, three launches:
-//   max pass:  every candidate still allowed is tested against the row chosen
-//              last (the presets on the first pass); survivors get their FP64
-//              cosine written to `cosv` (rejected ones -inf, permanently), and
-//              the maximum goes to an order-preserving 64-bit key (atomicMax);
-//   pick pass: candidates within the tolerance of the maximum compete on
-//              (norm key << 32 | index) (atomicMin);
-//   commit:    one thread decodes the winner and records it (or a dead end).
+// Per row:
+//   max32:  candidates still allowed (a byte mask) are tested against the row
+//           chosen last (rejections clear the mask for good); survivors get an
+//           FP32 cosine from per-group tables and the FP32 maximum is kept;
+//   max64:  candidates within kScreen of the FP32 maximum get the FP64
+//           cosine; the FP64 maximum is kept (order-preserving atomicMax);
+//   pick:   the same screened candidates within the 1e-12 tolerance of the
+//           FP64 maximum compete on (norm key << 32 | index) (atomicMin);
+//   commit: one thread decodes the winner and records it (or a dead end).
+// A candidate is the sum of its digit groups' table entries (groups of 4
+// digits, 3 for |P| >= 8): FP32 and FP64 partial dot products with the exact
+// DCT row, partial squared norms and partial dot products with the row
+// chosen last.  Presets are applied to the mask by filter passes first.
+//
+// Screening loses no candidate: the group partial products satisfy
+// sum |<c_g, d_g>| <= ||c|| ||d|| = ||d||, so the FP32 cosine (at most six
+// rounded table entries, five additions, one multiplication by a rounded
+// 1 / sqrt(n2)) is within 9 * 2^-24 < 5.4e-7 of the true one.  Every
+// candidate within the tie tolerance of the true maximum therefore lies
+// within 1.1e-6 + 1e-12 of the FP32 maximum, well inside kScreen = 1e-5.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -62,15 +74,41 @@ __host__ __device__ constexpr int group_entries() {
   return e;
 }
 
-// Shared-memory tables of one row's pass, per group g of G digits and per
-// digit combination c of that group: the FP64 partial dot product with the
-// exact DCT row, the partial squared norm and the partial dot product with
-// `against` (the row chosen last, or a preset).  A candidate is the sum of
-// its groups' entries.
+constexpr float kScreen = 1e-5f;
+
+__device__ __forceinline__ uint32_t order_key32(float v) {
+  const uint32_t b = __float_as_uint(v);
+  return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_value32(uint32_t k) {
+  return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Shared-memory tables of one pass, laid out after the 1/sqrt(n2) tables.
+struct Tables {
+  const double* inv64;
+  const float* inv32;
+  const double* d64;
+  const float* d32;
+  const int* n2;
+  const int* o;
+};
+
 template <int NP>
-__device__ __forceinline__ void build_tables(const SearchParams& sp, const int8_t* against_rev,
-                                             double* dtab, int* ntab, int* otab, int groups) {
+__device__ __forceinline__ Tables build_tables(const SearchParams& sp, const int8_t* against_rev,
+                                               unsigned char* raw, int groups) {
   constexpr int G = group_digits<NP>(), E = group_entries<NP>();
+  double* inv64 = reinterpret_cast<double*>(raw);
+  double* d64 = inv64 + (sp.max_n2 + 1);
+  float* inv32 = reinterpret_cast<float*>(d64 + groups * E);
+  float* d32 = inv32 + (sp.max_n2 + 1);
+  int* n2t = reinterpret_cast<int*>(d32 + groups * E);
+  int* ot = n2t + groups * E;
+  for (int q = threadIdx.x; q <= sp.max_n2; q += blockDim.x) {
+    const double v = q > 0 ? 1.0 / sqrt((double)q) : 0.0;
+    inv64[q] = v;
+    inv32[q] = (float)v;
+  }
   for (int e = threadIdx.x; e < groups * E; e += blockDim.x) {
     const int g = e / E;
     int c = e - g * E;
@@ -86,89 +124,128 @@ __device__ __forceinline__ void build_tables(const SearchParams& sp, const int8_
         o += v * (against_rev ? against_rev[k] : 0);
       }
     }
-    dtab[e] = d;
-    ntab[e] = n2;
-    otab[e] = o;
+    d64[e] = d;
+    d32[e] = (float)d;
+    n2t[e] = n2;
+    ot[e] = o;
+  }
+  return Tables{inv64, inv32, d64, d32, n2t, ot};
+}
+
+// Per-candidate sums over the digit groups.
+template <int NP, bool WITH_O, bool WITH_D64>
+__device__ __forceinline__ void sum_groups(uint32_t idx, int groups, const Tables& t, int& n2,
+                                           int& o, float& d32, double& d64) {
+  constexpr int E = group_entries<NP>();
+  n2 = 0;
+  o = 0;
+  d32 = 0.f;
+  d64 = 0.0;
+  for (int g = 0; g < groups; ++g) {
+    const uint32_t q = idx / E, c = idx - q * E;
+    idx = q;
+    n2 += t.n2[g * E + c];
+    if (WITH_O) o += t.o[g * E + c];
+    d32 += t.d32[g * E + c];
+    if (WITH_D64) d64 += t.d64[g * E + c];
   }
 }
 
-// Allowed-set initialisation and presets: cosv[i] = 0 for candidates that
-// are nonzero and orthogonal to the preset (or to nothing), -inf otherwise.
+// Mask initialisation and presets: allowed = nonzero and orthogonal to the
+// preset (init: to nothing).
 template <int NP>
-__global__ void __launch_bounds__(256) search_filter(SearchParams sp, double* __restrict__ cosv,
+__global__ void __launch_bounds__(256) search_filter(SearchParams sp, uint8_t* __restrict__ allowed,
                                                      int preset, int init) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int E = group_entries<NP>(), G = group_digits<NP>();
+  constexpr int G = group_digits<NP>();
   const int groups = (sp.N + G - 1) / G;
-  double* dtab = reinterpret_cast<double*>(smem_raw) + (sp.max_n2 + 1);
-  int* ntab = reinterpret_cast<int*>(dtab + groups * E);
-  int* otab = ntab + groups * E;
   __shared__ int8_t rev[kSearchMaxN];
   if (threadIdx.x < kSearchMaxN)
-    rev[threadIdx.x] = (preset >= 0 && threadIdx.x < sp.N) ? sp.fixed[preset][sp.N - 1 - threadIdx.x] : 0;
+    rev[threadIdx.x] =
+        (preset >= 0 && (int)threadIdx.x < sp.N) ? sp.fixed[preset][sp.N - 1 - threadIdx.x] : 0;
   __syncthreads();
-  build_tables<NP>(sp, rev, dtab, ntab, otab, groups);
+  const Tables t = build_tables<NP>(sp, rev, smem_raw, groups);
   __syncthreads();
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
        i += gridDim.x * blockDim.x) {
-    if (!init && cosv[i] == -INFINITY) continue;
-    uint32_t idx = i;
-    int n2 = 0, o = 0;
-    for (int g = 0; g < groups; ++g) {
-      const uint32_t q = idx / E, c = idx - q * E;
-      idx = q;
-      n2 += ntab[g * E + c];
-      o += otab[g * E + c];
-    }
+    if (!init && !allowed[i]) continue;
+    int n2, o;
+    float d32;
+    double d64;
+    sum_groups<NP, true, false>(i, groups, t, n2, o, d32, d64);
     const bool ok = n2 > 0 && o == 0;
-    if (init || !ok) cosv[i] = ok ? 0.0 : -INFINITY;
+    if (init || !ok) allowed[i] = ok ? 1 : 0;
   }
 }
 
 template <int NP>
-__global__ void __launch_bounds__(256) search_max(SearchParams sp, SearchState* __restrict__ st,
-                                                  double* __restrict__ cosv, int first) {
+__global__ void __launch_bounds__(256) search_max32(SearchParams sp, SearchState* __restrict__ st,
+                                                    uint8_t* __restrict__ allowed, int first) {
   if (st->dead) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int E = group_entries<NP>(), G = group_digits<NP>();
+  constexpr int G = group_digits<NP>();
   const int groups = (sp.N + G - 1) / G;
-  double* inv_norm = reinterpret_cast<double*>(smem_raw);  // 1 / sqrt(n2), n2 = 0..max_n2
-  double* dtab = inv_norm + (sp.max_n2 + 1);
-  int* ntab = reinterpret_cast<int*>(dtab + groups * E);
-  int* otab = ntab + groups * E;
   __shared__ int8_t rev[kSearchMaxN];
-  __shared__ unsigned long long warp_best[8];
+  __shared__ uint32_t warp_best[8];
   if (threadIdx.x < kSearchMaxN)
-    rev[threadIdx.x] = (!first && threadIdx.x < sp.N) ? st->last_row[sp.N - 1 - threadIdx.x] : 0;
-  for (int q = threadIdx.x; q <= sp.max_n2; q += blockDim.x)
-    inv_norm[q] = q > 0 ? 1.0 / sqrt((double)q) : 0.0;
+    rev[threadIdx.x] = (!first && (int)threadIdx.x < sp.N) ? st->last_row[sp.N - 1 - threadIdx.x] : 0;
   __syncthreads();
-  build_tables<NP>(sp, first ? nullptr : rev, dtab, ntab, otab, groups);
+  const Tables t = build_tables<NP>(sp, first ? nullptr : rev, smem_raw, groups);
   __syncthreads();
-  unsigned long long best = 0ull;  // below every key of a finite value
+  uint32_t best = 0u;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
        i += gridDim.x * blockDim.x) {
-    if (cosv[i] == -INFINITY) continue;
-    uint32_t idx = i;
-    int n2 = 0, o = 0;
-    double dot = 0.0;
-    for (int g = 0; g < groups; ++g) {
-      const uint32_t q = idx / E, c = idx - q * E;
-      idx = q;
-      n2 += ntab[g * E + c];
-      o += otab[g * E + c];
-      dot += dtab[g * E + c];
+    if (!allowed[i]) continue;
+    int n2, o;
+    float d32;
+    double d64;
+    sum_groups<NP, true, false>(i, groups, t, n2, o, d32, d64);
+    if (o != 0) {  // not orthogonal to the row chosen last: rejected for good
+      allowed[i] = 0;
+      continue;
     }
-    double c = -INFINITY;
-    if (o == 0) {  // nonzero and orthogonal to the presets: filtered before
-      c = dot * inv_norm[n2];
-      const unsigned long long key = order_key(c);
-      best = key > best ? key : best;
-    }
-    cosv[i] = c;
+    const uint32_t key = order_key32(d32 * t.inv32[n2]);
+    best = key > best ? key : best;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long other = __shfl_down_sync(0xffffffffu, best, o);
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint32_t other = __shfl_down_sync(0xffffffffu, best, off);
+    best = other > best ? other : best;
+  }
+  if ((threadIdx.x & 31) == 0) warp_best[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t b = 0u;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = warp_best[w] > b ? warp_best[w] : b;
+    if (b) atomicMax(&st->best32, b);
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(256) search_max64(SearchParams sp, SearchState* __restrict__ st,
+                                                    const uint8_t* __restrict__ allowed) {
+  if (st->dead || st->best32 == 0u) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int G = group_digits<NP>();
+  const int groups = (sp.N + G - 1) / G;
+  __shared__ unsigned long long warp_best[8];
+  const Tables t = build_tables<NP>(sp, nullptr, smem_raw, groups);
+  __syncthreads();
+  const float lim32 = key_value32(st->best32) - kScreen;
+  unsigned long long best = 0ull;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
+       i += gridDim.x * blockDim.x) {
+    if (!allowed[i]) continue;
+    int n2, o;
+    float d32;
+    double d64;
+    sum_groups<NP, false, false>(i, groups, t, n2, o, d32, d64);
+    if (!(d32 * t.inv32[n2] >= lim32)) continue;
+    sum_groups<NP, false, true>(i, groups, t, n2, o, d32, d64);
+    const unsigned long long key = order_key(d64 * t.inv64[n2]);
+    best = key > best ? key : best;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long other = __shfl_down_sync(0xffffffffu, best, off);
     best = other > best ? other : best;
   }
   if ((threadIdx.x & 31) == 0) warp_best[threadIdx.x >> 5] = best;
@@ -182,25 +259,33 @@ __global__ void __launch_bounds__(256) search_max(SearchParams sp, SearchState* 
 
 template <int NP>
 __global__ void __launch_bounds__(256) search_pick(SearchParams sp, SearchState* __restrict__ st,
-                                                   const double* __restrict__ cosv) {
+                                                   const uint8_t* __restrict__ allowed) {
   if (st->dead || st->best_key == 0ull) return;
-  const double lim = key_value(st->best_key) - kSearchTieTol;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int G = group_digits<NP>();
+  const int groups = (sp.N + G - 1) / G;
+  const Tables t = build_tables<NP>(sp, nullptr, smem_raw, groups);
+  __syncthreads();
+  const float lim32 = key_value32(st->best32) - kScreen;
+  const double lim64 = key_value(st->best_key) - kSearchTieTol;
   unsigned long long pick = ~0ull;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
        i += gridDim.x * blockDim.x) {
-    if (!(cosv[i] >= lim)) continue;
-    int v[kSearchMaxN];
-    decode<NP>(i, sp.N, sp, v);
-    int n2 = 0;
-#pragma unroll
-    for (int k = 0; k < kSearchMaxN; ++k) n2 += v[k] * v[k];
+    if (!allowed[i]) continue;
+    int n2, o;
+    float d32;
+    double d64;
+    sum_groups<NP, false, false>(i, groups, t, n2, o, d32, d64);
+    if (!(d32 * t.inv32[n2] >= lim32)) continue;
+    sum_groups<NP, false, true>(i, groups, t, n2, o, d32, d64);
+    if (!(d64 * t.inv64[n2] >= lim64)) continue;
     const unsigned long long nk = sp.tie_large ? (unsigned long long)(0xffffff - n2)
                                                : (unsigned long long)n2;
     const unsigned long long key = (nk << 32) | i;
     pick = key < pick ? key : pick;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long other = __shfl_down_sync(0xffffffffu, pick, o);
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long other = __shfl_down_sync(0xffffffffu, pick, off);
     pick = other < pick ? other : pick;
   }
   if ((threadIdx.x & 31) == 0 && pick != ~0ull) atomicMin(&st->pick_key, pick);
@@ -209,7 +294,7 @@ __global__ void __launch_bounds__(256) search_pick(SearchParams sp, SearchState*
 template <int NP>
 __global__ void search_commit(SearchParams sp, SearchState* __restrict__ st, int slot) {
   if (st->dead) return;
-  if (st->best_key == 0ull || st->pick_key == ~0ull) {
+  if (st->best32 == 0u || st->best_key == 0ull || st->pick_key == ~0ull) {
     st->dead = 1;
     return;
   }
@@ -221,50 +306,51 @@ __global__ void search_commit(SearchParams sp, SearchState* __restrict__ st, int
   for (int k = 0; k < kSearchMaxN; ++k)
     if (k < sp.N) st->last_row[sp.N - 1 - k] = (int8_t)v[k];
   st->n_done = slot + 1;
+  st->best32 = 0u;
   st->best_key = 0ull;
   st->pick_key = ~0ull;
 }
 
+constexpr int kSearchMaxSmem = 200 * 1024;
+
 template <int NP>
 size_t table_bytes(const SearchParams& sp) {
   constexpr int G = group_digits<NP>();
-  return sizeof(double) * (size_t)(sp.max_n2 + 1) +
-         (size_t)((sp.N + G - 1) / G) * group_entries<NP>() * (sizeof(double) + 2 * sizeof(int));
+  return (size_t)(sp.max_n2 + 1) * 12 +
+         (size_t)((sp.N + G - 1) / G) * group_entries<NP>() * 20;
 }
 
 template <int NP>
-cudaError_t enqueue_row(const SearchParams& sp, SearchState* st, double* cosv, int first,
+cudaError_t enqueue_row(const SearchParams& sp, SearchState* st, uint8_t* allowed, int first,
                         int slot, int grid, cudaStream_t s) {
   const size_t smem = table_bytes<NP>(sp);
-  // the opt-in shared-memory limit is raised once per instantiation, to the
-  // largest table any accepted (alphabet, N) needs
+  if (smem > (size_t)kSearchMaxSmem) return cudaErrorInvalidValue;
+  // the opt-in shared-memory limit is raised once per instantiation
   static int limit_set = 0;
   if (!limit_set) {
-    constexpr int kMaxSmem = 140 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(search_max<NP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(search_filter<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kMaxSmem);
+    cudaError_t e = cudaSuccess;
+    for (const void* f : {(const void*)search_filter<NP>, (const void*)search_max32<NP>,
+                          (const void*)search_max64<NP>, (const void*)search_pick<NP>})
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSearchMaxSmem);
     if (e != cudaSuccess) return e;
     limit_set = 1;
   }
-  if (smem > 140 * 1024) return cudaErrorInvalidValue;
   if (first) {
-    // allowed set: nonzero candidates orthogonal to every preset
-    search_filter<NP><<<grid, 256, smem, s>>>(sp, cosv, -1, 1);
-    for (int f = 0; f < sp.n_fixed; ++f) search_filter<NP><<<grid, 256, smem, s>>>(sp, cosv, f, 0);
+    search_filter<NP><<<grid, 256, smem, s>>>(sp, allowed, -1, 1);
+    for (int f = 0; f < sp.n_fixed; ++f) search_filter<NP><<<grid, 256, smem, s>>>(sp, allowed, f, 0);
   }
-  search_max<NP><<<grid, 256, smem, s>>>(sp, st, cosv, first);
-  search_pick<NP><<<grid, 256, 0, s>>>(sp, st, cosv);
+  search_max32<NP><<<grid, 256, smem, s>>>(sp, st, allowed, first);
+  search_max64<NP><<<grid, 256, smem, s>>>(sp, st, allowed);
+  search_pick<NP><<<grid, 256, smem, s>>>(sp, st, allowed);
   search_commit<NP><<<1, 1, 0, s>>>(sp, st, slot);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t enqueue_search_row(const SearchParams& sp, SearchState* st, double* cosv, int first,
-                               int slot, cudaStream_t s) {
+cudaError_t enqueue_search_row(const SearchParams& sp, SearchState* st, uint8_t* allowed,
+                               int first, int slot, cudaStream_t s) {
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -272,14 +358,14 @@ cudaError_t enqueue_search_row(const SearchParams& sp, SearchState* st, double* 
   if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
   if (grid < 1) grid = 1;
   switch (sp.np) {
-    case 2: return enqueue_row<2>(sp, st, cosv, first, slot, (int)grid, s);
-    case 3: return enqueue_row<3>(sp, st, cosv, first, slot, (int)grid, s);
-    case 4: return enqueue_row<4>(sp, st, cosv, first, slot, (int)grid, s);
-    case 5: return enqueue_row<5>(sp, st, cosv, first, slot, (int)grid, s);
-    case 6: return enqueue_row<6>(sp, st, cosv, first, slot, (int)grid, s);
-    case 7: return enqueue_row<7>(sp, st, cosv, first, slot, (int)grid, s);
-    case 8: return enqueue_row<8>(sp, st, cosv, first, slot, (int)grid, s);
-    case 9: return enqueue_row<9>(sp, st, cosv, first, slot, (int)grid, s);
+    case 2: return enqueue_row<2>(sp, st, allowed, first, slot, (int)grid, s);
+    case 3: return enqueue_row<3>(sp, st, allowed, first, slot, (int)grid, s);
+    case 4: return enqueue_row<4>(sp, st, allowed, first, slot, (int)grid, s);
+    case 5: return enqueue_row<5>(sp, st, allowed, first, slot, (int)grid, s);
+    case 6: return enqueue_row<6>(sp, st, allowed, first, slot, (int)grid, s);
+    case 7: return enqueue_row<7>(sp, st, allowed, first, slot, (int)grid, s);
+    case 8: return enqueue_row<8>(sp, st, allowed, first, slot, (int)grid, s);
+    case 9: return enqueue_row<9>(sp, st, allowed, first, slot, (int)grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

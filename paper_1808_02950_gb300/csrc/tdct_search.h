@@ -23,18 +23,19 @@ struct SearchParams {
 };
 
 struct SearchState {
-  unsigned long long best_key;  // order-preserving key of the best cosine (0 = none yet)
+  unsigned long long best_key;  // order-preserving key of the best FP64 cosine (0 = none yet)
   unsigned long long pick_key;  // (norm key << 32) | index of the winner (~0 = none yet)
+  uint32_t best32;              // order-preserving key of the best FP32 cosine (0 = none yet)
   int32_t dead;                 // a row had no allowed candidate
   int32_t n_done;               // rows committed so far
   int8_t last_row[kSearchMaxN];
   uint32_t chosen[kSearchMaxN];  // winner index per searched row
 };
 
-// Enqueue the max / pick / commit launches of one searched row.  `first`:
-// test against the presets (and start from all candidates); later rows test
-// against the row chosen last and skip candidates already rejected in cosv.
-cudaError_t enqueue_search_row(const SearchParams& sp, SearchState* st, double* cosv, int first,
-                               int slot, cudaStream_t s);
+// Enqueue the launches of one searched row.  `first`: build the allowed
+// mask (one byte per candidate) from the presets; later rows test against
+// the row chosen last and clear the mask of the candidates it rejects.
+cudaError_t enqueue_search_row(const SearchParams& sp, SearchState* st, uint8_t* allowed,
+                               int first, int slot, cudaStream_t s);
 
 }  // namespace tdct
