@@ -151,8 +151,38 @@ __device__ __forceinline__ void sum_groups(uint32_t idx, int groups, const Table
   }
 }
 
-// Mask initialisation and presets: allowed = nonzero and orthogonal to the
-// preset (init: to nothing).
+// Visits the allowed candidates: each thread loads 16 mask bytes at a time
+// and skips all-zero words (the mask is padded to whole words with zeros).
+// f(i) returns false to clear candidate i's byte (written back if WRITE).
+template <bool WRITE, class F>
+__device__ __forceinline__ void for_each_allowed(uint8_t* allowed, uint32_t total, F&& f) {
+  const uint32_t words = (total + 15u) / 16u;
+  uint4* mw = reinterpret_cast<uint4*>(allowed);
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < words;
+       w += gridDim.x * blockDim.x) {
+    const uint4 m = mw[w];
+    uint32_t part[4] = {m.x, m.y, m.z, m.w};
+    if ((part[0] | part[1] | part[2] | part[3]) == 0u) continue;
+    bool changed = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t b = part[q];
+      while (b) {
+        const int sh = (__ffs(b) - 1) & ~7;
+        b &= ~(0xffu << sh);
+        if (!f(w * 16u + (uint32_t)(q * 4 + (sh >> 3)))) {
+          part[q] &= ~(0xffu << sh);
+          changed = true;
+        }
+      }
+    }
+    if (WRITE && changed) mw[w] = make_uint4(part[0], part[1], part[2], part[3]);
+  }
+}
+
+// Mask initialisation (init: allowed = nonzero, padding bytes zero) and
+// presets (allowed candidates not orthogonal to preset row `preset` are
+// cleared).
 template <int NP>
 __global__ void __launch_bounds__(256) search_filter(SearchParams sp, uint8_t* __restrict__ allowed,
                                                      int preset, int init) {
@@ -166,16 +196,31 @@ __global__ void __launch_bounds__(256) search_filter(SearchParams sp, uint8_t* _
   __syncthreads();
   const Tables t = build_tables<NP>(sp, rev, smem_raw, groups);
   __syncthreads();
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
-       i += gridDim.x * blockDim.x) {
-    if (!init && !allowed[i]) continue;
+  if (init) {
+    const uint32_t words = (sp.total + 15u) / 16u;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < words;
+         w += gridDim.x * blockDim.x) {
+      uint32_t part[4] = {0u, 0u, 0u, 0u};
+      for (int j = 0; j < 16; ++j) {
+        const uint32_t i = w * 16u + (uint32_t)j;
+        if (i >= sp.total) break;
+        int n2, o;
+        float d32;
+        double d64;
+        sum_groups<NP, false, false>(i, groups, t, n2, o, d32, d64);
+        if (n2 > 0) part[j >> 2] |= 1u << ((j & 3) * 8);
+      }
+      reinterpret_cast<uint4*>(allowed)[w] = make_uint4(part[0], part[1], part[2], part[3]);
+    }
+    return;
+  }
+  for_each_allowed<true>(allowed, sp.total, [&](uint32_t i) {
     int n2, o;
     float d32;
     double d64;
     sum_groups<NP, true, false>(i, groups, t, n2, o, d32, d64);
-    const bool ok = n2 > 0 && o == 0;
-    if (init || !ok) allowed[i] = ok ? 1 : 0;
-  }
+    return o == 0;
+  });
 }
 
 template <int NP>
@@ -193,20 +238,16 @@ __global__ void __launch_bounds__(256) search_max32(SearchParams sp, SearchState
   const Tables t = build_tables<NP>(sp, first ? nullptr : rev, smem_raw, groups);
   __syncthreads();
   uint32_t best = 0u;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
-       i += gridDim.x * blockDim.x) {
-    if (!allowed[i]) continue;
+  for_each_allowed<true>(allowed, sp.total, [&](uint32_t i) {
     int n2, o;
     float d32;
     double d64;
     sum_groups<NP, true, false>(i, groups, t, n2, o, d32, d64);
-    if (o != 0) {  // not orthogonal to the row chosen last: rejected for good
-      allowed[i] = 0;
-      continue;
-    }
+    if (o != 0) return false;  // not orthogonal to the row chosen last: rejected for good
     const uint32_t key = order_key32(d32 * t.inv32[n2]);
     best = key > best ? key : best;
-  }
+    return true;
+  });
   for (int off = 16; off > 0; off >>= 1) {
     const uint32_t other = __shfl_down_sync(0xffffffffu, best, off);
     best = other > best ? other : best;
@@ -222,7 +263,7 @@ __global__ void __launch_bounds__(256) search_max32(SearchParams sp, SearchState
 
 template <int NP>
 __global__ void __launch_bounds__(256) search_max64(SearchParams sp, SearchState* __restrict__ st,
-                                                    const uint8_t* __restrict__ allowed) {
+                                                    uint8_t* __restrict__ allowed) {
   if (st->dead || st->best32 == 0u) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int G = group_digits<NP>();
@@ -232,18 +273,18 @@ __global__ void __launch_bounds__(256) search_max64(SearchParams sp, SearchState
   __syncthreads();
   const float lim32 = key_value32(st->best32) - kScreen;
   unsigned long long best = 0ull;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
-       i += gridDim.x * blockDim.x) {
-    if (!allowed[i]) continue;
+  for_each_allowed<false>(allowed, sp.total, [&](uint32_t i) {
     int n2, o;
     float d32;
     double d64;
     sum_groups<NP, false, false>(i, groups, t, n2, o, d32, d64);
-    if (!(d32 * t.inv32[n2] >= lim32)) continue;
-    sum_groups<NP, false, true>(i, groups, t, n2, o, d32, d64);
-    const unsigned long long key = order_key(d64 * t.inv64[n2]);
-    best = key > best ? key : best;
-  }
+    if (d32 * t.inv32[n2] >= lim32) {
+      sum_groups<NP, false, true>(i, groups, t, n2, o, d32, d64);
+      const unsigned long long key = order_key(d64 * t.inv64[n2]);
+      best = key > best ? key : best;
+    }
+    return true;
+  });
   for (int off = 16; off > 0; off >>= 1) {
     const unsigned long long other = __shfl_down_sync(0xffffffffu, best, off);
     best = other > best ? other : best;
@@ -259,7 +300,7 @@ __global__ void __launch_bounds__(256) search_max64(SearchParams sp, SearchState
 
 template <int NP>
 __global__ void __launch_bounds__(256) search_pick(SearchParams sp, SearchState* __restrict__ st,
-                                                   const uint8_t* __restrict__ allowed) {
+                                                   uint8_t* __restrict__ allowed) {
   if (st->dead || st->best_key == 0ull) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int G = group_digits<NP>();
@@ -269,21 +310,22 @@ __global__ void __launch_bounds__(256) search_pick(SearchParams sp, SearchState*
   const float lim32 = key_value32(st->best32) - kScreen;
   const double lim64 = key_value(st->best_key) - kSearchTieTol;
   unsigned long long pick = ~0ull;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < sp.total;
-       i += gridDim.x * blockDim.x) {
-    if (!allowed[i]) continue;
+  for_each_allowed<false>(allowed, sp.total, [&](uint32_t i) {
     int n2, o;
     float d32;
     double d64;
     sum_groups<NP, false, false>(i, groups, t, n2, o, d32, d64);
-    if (!(d32 * t.inv32[n2] >= lim32)) continue;
-    sum_groups<NP, false, true>(i, groups, t, n2, o, d32, d64);
-    if (!(d64 * t.inv64[n2] >= lim64)) continue;
-    const unsigned long long nk = sp.tie_large ? (unsigned long long)(0xffffff - n2)
-                                               : (unsigned long long)n2;
-    const unsigned long long key = (nk << 32) | i;
-    pick = key < pick ? key : pick;
-  }
+    if (d32 * t.inv32[n2] >= lim32) {
+      sum_groups<NP, false, true>(i, groups, t, n2, o, d32, d64);
+      if (d64 * t.inv64[n2] >= lim64) {
+        const unsigned long long nk = sp.tie_large ? (unsigned long long)(0xffffff - n2)
+                                                   : (unsigned long long)n2;
+        const unsigned long long key = (nk << 32) | i;
+        pick = key < pick ? key : pick;
+      }
+    }
+    return true;
+  });
   for (int off = 16; off > 0; off >>= 1) {
     const unsigned long long other = __shfl_down_sync(0xffffffffu, pick, off);
     pick = other < pick ? other : pick;
@@ -354,7 +396,7 @@ cudaError_t enqueue_search_row(const SearchParams& sp, SearchState* st, uint8_t*
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t grid = ((int64_t)sp.total + 255) / 256;
+  int64_t grid = ((int64_t)sp.total + 16 * 256 - 1) / (16 * 256);  // 16 candidates per thread
   if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
   if (grid < 1) grid = 1;
   switch (sp.np) {
