@@ -283,7 +283,8 @@ int tdct_ssim_batched(const tdct_ssim_plane* planes, int nplanes, double* d_mssi
  *   complete    host output: 1, or 0 when some row had no orthogonal
  *               candidate left (the rows before it are in T_out)
  * Synchronous: the call waits for its work on `stream`.  Device scratch of
- * np^N bytes (one per candidate) comes from the stream-ordered pool.
+ * np^N bytes (one per candidate) plus 1 MiB comes from the stream-ordered
+ * pool.
  * Errors: TDCT_EINVAL (arguments), TDCT_EUNSUPPORTED (np^N > 2^31),
  * TDCT_ENOMEM, TDCT_ECUDA.
  */
@@ -349,6 +350,15 @@ int tdct_sync_status(tdct_stream_t stream);
  * leaves the context usable.
  */
 int tdct_debug_inject_wait_timeout(int enable);
+
+/*
+ * Test hook for tdct_search (no counterpart in the paper).  Sets the capacity
+ * of the per-row list of candidates that pass the FP32 screen; a row with more
+ * such candidates falls back to a second full scan.  cap outside [0, 65536]
+ * restores the default (65536).  The result of tdct_search does not depend on
+ * it; the test suite uses a small cap to run the fallback scan.
+ */
+int tdct_debug_search_hit_cap(int cap);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* tdct_last_error(void);

@@ -38,6 +38,7 @@ EXPORTS = (
     "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_config",
     "tdct_plan_destroy",
     "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
+    "tdct_debug_search_hit_cap",
     "tdct_last_error", "tdct_version",
 )
 
@@ -94,6 +95,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_dct_codec_error.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp, vp, i64, vp, vp, vp]
     L.tdct_sync_status.argtypes = [vp]
     L.tdct_debug_inject_wait_timeout.argtypes = [i32]
+    L.tdct_debug_search_hit_cap.argtypes = [i32]
     L.tdct_last_error.restype = ctypes.c_char_p
     L.tdct_version.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -333,6 +335,10 @@ def tdct_dct_codec_error(img, r: int, sse, precision=TDCT_FP32, coef=None, recon
 
 def tdct_debug_inject_wait_timeout(enable: bool = True) -> None:
     _check(load().tdct_debug_inject_wait_timeout(1 if enable else 0))
+
+
+def tdct_debug_search_hit_cap(cap: int = -1) -> None:
+    _check(load().tdct_debug_search_hit_cap(int(cap)))
 
 
 def tdct_sync_status(stream=None) -> None:

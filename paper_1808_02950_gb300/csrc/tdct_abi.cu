@@ -180,6 +180,7 @@ int check_r(int r) {
 // One-shot test hook: the next codec launch withholds one bulk copy so that
 // its bounded wait runs out (see tdct_debug_inject_wait_timeout).
 std::atomic<int> g_inject_timeout{0};
+std::atomic<int> g_search_hit_cap{kSearchHitCap};
 
 int* status_word() {
   static void* addr[256] = {};
@@ -1313,13 +1314,17 @@ int tdct_search(int N, const int8_t* alphabet, int np, const int32_t* order, int
   sp.total = (uint32_t)total;
   sp.n_fixed = n_fixed;
   sp.tie_large = tie;
+  sp.hit_cap = g_search_hit_cap.load();
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void* block = nullptr;
   const size_t bytes_mask = round_up((size_t)total, 256);
-  cudaError_t e = cudaMallocAsync(&block, bytes_mask + sizeof(SearchState), s);
+  const size_t bytes_hits = sizeof(SearchHit) * (size_t)kSearchHitCap;
+  cudaError_t e = cudaMallocAsync(&block, bytes_mask + bytes_hits + sizeof(SearchState), s);
   if (e != cudaSuccess) return fail(TDCT_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e));
   uint8_t* allowed = static_cast<uint8_t*>(block);
-  SearchState* st = reinterpret_cast<SearchState*>(static_cast<char*>(block) + bytes_mask);
+  SearchHit* hits = reinterpret_cast<SearchHit*>(static_cast<char*>(block) + bytes_mask);
+  SearchState* st =
+      reinterpret_cast<SearchState*>(static_cast<char*>(block) + bytes_mask + bytes_hits);
   SearchState init;
   std::memset(&init, 0, sizeof init);
   init.pick_key = ~0ull;
@@ -1332,7 +1337,7 @@ int tdct_search(int N, const int8_t* alphabet, int np, const int32_t* order, int
       const double ck = k == 0 ? std::sqrt(1.0 / N) : std::sqrt(2.0 / N);
       sp.crow_rev[N - 1 - j] = ck * std::cos(M_PI * (2.0 * j + 1.0) * k / (2.0 * N));
     }
-    e = enqueue_search_row(sp, st, allowed, i == 0, i, s);
+    e = enqueue_search_row(sp, st, allowed, hits, i == 0, i, s);
   }
   SearchState out;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&out, st, sizeof out, cudaMemcpyDeviceToHost, s);
@@ -1384,6 +1389,11 @@ int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dty
 
 int tdct_debug_inject_wait_timeout(int enable) {
   g_inject_timeout.store(enable ? 1 : 0);
+  return TDCT_OK;
+}
+
+int tdct_debug_search_hit_cap(int cap) {
+  g_search_hit_cap.store(cap >= 0 && cap <= kSearchHitCap ? cap : kSearchHitCap);
   return TDCT_OK;
 }
 

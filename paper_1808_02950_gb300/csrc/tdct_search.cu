@@ -15,9 +15,11 @@
 //           chosen last (rejections clear the mask for good); survivors get an
 //           FP32 cosine from per-group tables and the FP32 maximum is kept;
 //   max64:  candidates within kScreen of the FP32 maximum get the FP64
-//           cosine; the FP64 maximum is kept (order-preserving atomicMax);
-//   pick:   the same screened candidates within the 1e-12 tolerance of the
-//           FP64 maximum compete on (norm key << 32 | index) (atomicMin);
+//           cosine; the FP64 maximum is kept (order-preserving atomicMax)
+//           and the screened candidates go to a small hit list;
+//   pick:   the screened candidates within the 1e-12 tolerance of the FP64
+//           maximum compete on (norm key << 32 | index) (atomicMin), read
+//           from the hit list (a full rescan only if the list overflowed);
 //   commit: one thread decodes the winner and records it (or a dead end).
 // A candidate is the sum of its digit groups' table entries (groups of 4
 // digits, 3 for |P| >= 8): FP32 and FP64 partial dot products with the exact
@@ -132,45 +134,94 @@ __device__ __forceinline__ Tables build_tables(const SearchParams& sp, const int
   return Tables{inv64, inv32, d64, d32, n2t, ot};
 }
 
-// Per-candidate sums over the digit groups.
-template <int NP, bool WITH_O, bool WITH_D64>
-__device__ __forceinline__ void sum_groups(uint32_t idx, int groups, const Tables& t, int& n2,
-                                           int& o, float& d32, double& d64) {
+// Sums over the digit groups above the lowest one (group 0), for hi = i / E.
+struct Upper {
+  int n2, o;
+  float d32;
+};
+
+template <int NP, bool WITH_O>
+__device__ __forceinline__ Upper upper_sums(uint32_t hi, int groups, const Tables& t) {
   constexpr int E = group_entries<NP>();
-  n2 = 0;
-  o = 0;
-  d32 = 0.f;
-  d64 = 0.0;
-  for (int g = 0; g < groups; ++g) {
-    const uint32_t q = idx / E, c = idx - q * E;
-    idx = q;
-    n2 += t.n2[g * E + c];
-    if (WITH_O) o += t.o[g * E + c];
-    d32 += t.d32[g * E + c];
-    if (WITH_D64) d64 += t.d64[g * E + c];
+  Upper u{0, 0, 0.f};
+  for (int g = 1; g < groups; ++g) {
+    const uint32_t q = hi / E, c = hi - q * E;
+    hi = q;
+    u.n2 += t.n2[g * E + c];
+    if (WITH_O) u.o += t.o[g * E + c];
+    u.d32 += t.d32[g * E + c];
   }
+  return u;
 }
 
-// Visits the allowed candidates: each thread loads 16 mask bytes at a time
-// and skips all-zero words (the mask is padded to whole words with zeros).
-// f(i) returns false to clear candidate i's byte (written back if WRITE).
-template <bool WRITE, class F>
-__device__ __forceinline__ void for_each_allowed(uint8_t* allowed, uint32_t total, F&& f) {
-  const uint32_t words = (total + 15u) / 16u;
+// One visited candidate: index, squared norm, dot product with the row
+// chosen last (when asked for), FP32 dot product with the DCT row; d64()
+// forms the FP64 dot product (only for the few candidates that need it).
+template <int NP>
+struct Cand {
+  uint32_t i, hi;
+  int c, groups;
+  int n2, o;
+  float d32;
+  const Tables* t;
+  __device__ __forceinline__ double d64() const {
+    constexpr int E = group_entries<NP>();
+    double d = t->d64[c];
+    uint32_t h = hi;
+    for (int g = 1; g < groups; ++g) {
+      const uint32_t q = h / E, e = h - q * E;
+      h = q;
+      d += t->d64[g * E + e];
+    }
+    return d;
+  }
+};
+
+// Visits the allowed candidates.  Each thread loads 16 mask bytes at a time
+// and skips all-zero words (the mask is padded to whole words with zeros);
+// the upper groups' sums are formed once per word (twice when the word
+// crosses a group-0 boundary: E >= 16, so at most once).  f(c) returns false
+// to clear the candidate's byte (written back when WRITE).
+template <int NP, bool WRITE, bool WITH_O, class F>
+__device__ __forceinline__ void visit_allowed(uint8_t* allowed, const SearchParams& sp, int groups,
+                                              const Tables& t, F&& f) {
+  constexpr int E = group_entries<NP>();
+  const uint32_t words = (sp.total + 15u) / 16u;
   uint4* mw = reinterpret_cast<uint4*>(allowed);
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < words;
        w += gridDim.x * blockDim.x) {
     const uint4 m = mw[w];
     uint32_t part[4] = {m.x, m.y, m.z, m.w};
     if ((part[0] | part[1] | part[2] | part[3]) == 0u) continue;
-    bool changed = false;
+    const uint32_t base = w * 16u, hi = base / E;
+    const int c0 = (int)(base - hi * E);
+    Upper u = upper_sums<NP, WITH_O>(hi, groups, t);
+    bool crossed = false, changed = false;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint32_t b = part[q];
       while (b) {
         const int sh = (__ffs(b) - 1) & ~7;
         b &= ~(0xffu << sh);
-        if (!f(w * 16u + (uint32_t)(q * 4 + (sh >> 3)))) {
+        const int j = q * 4 + (sh >> 3);
+        int c = c0 + j;
+        if (c >= E) {  // candidates are visited in increasing order
+          if (!crossed) {
+            u = upper_sums<NP, WITH_O>(hi + 1, groups, t);
+            crossed = true;
+          }
+          c -= E;
+        }
+        Cand<NP> cd;
+        cd.i = base + (uint32_t)j;
+        cd.hi = crossed ? hi + 1 : hi;
+        cd.c = c;
+        cd.groups = groups;
+        cd.n2 = u.n2 + t.n2[c];
+        cd.o = WITH_O ? u.o + t.o[c] : 0;
+        cd.d32 = u.d32 + t.d32[c];
+        cd.t = &t;
+        if (!f(cd)) {
           part[q] &= ~(0xffu << sh);
           changed = true;
         }
@@ -187,7 +238,7 @@ template <int NP>
 __global__ void __launch_bounds__(256) search_filter(SearchParams sp, uint8_t* __restrict__ allowed,
                                                      int preset, int init) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int G = group_digits<NP>();
+  constexpr int G = group_digits<NP>(), E = group_entries<NP>();
   const int groups = (sp.N + G - 1) / G;
   __shared__ int8_t rev[kSearchMaxN];
   if (threadIdx.x < kSearchMaxN)
@@ -200,27 +251,23 @@ __global__ void __launch_bounds__(256) search_filter(SearchParams sp, uint8_t* _
     const uint32_t words = (sp.total + 15u) / 16u;
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < words;
          w += gridDim.x * blockDim.x) {
+      const uint32_t base = w * 16u, hi = base / E;
+      const int c0 = (int)(base - hi * E);
+      const int n2a = upper_sums<NP, false>(hi, groups, t).n2;
+      const int n2b = upper_sums<NP, false>(hi + 1, groups, t).n2;
       uint32_t part[4] = {0u, 0u, 0u, 0u};
       for (int j = 0; j < 16; ++j) {
-        const uint32_t i = w * 16u + (uint32_t)j;
-        if (i >= sp.total) break;
-        int n2, o;
-        float d32;
-        double d64;
-        sum_groups<NP, false, false>(i, groups, t, n2, o, d32, d64);
+        if (base + (uint32_t)j >= sp.total) break;
+        const int c = c0 + j;
+        const int n2 = c < E ? n2a + t.n2[c] : n2b + t.n2[c - E];
         if (n2 > 0) part[j >> 2] |= 1u << ((j & 3) * 8);
       }
       reinterpret_cast<uint4*>(allowed)[w] = make_uint4(part[0], part[1], part[2], part[3]);
     }
     return;
   }
-  for_each_allowed<true>(allowed, sp.total, [&](uint32_t i) {
-    int n2, o;
-    float d32;
-    double d64;
-    sum_groups<NP, true, false>(i, groups, t, n2, o, d32, d64);
-    return o == 0;
-  });
+  visit_allowed<NP, true, true>(allowed, sp, groups, t,
+                                [&](const Cand<NP>& c) { return c.o == 0; });
 }
 
 template <int NP>
@@ -238,13 +285,9 @@ __global__ void __launch_bounds__(256) search_max32(SearchParams sp, SearchState
   const Tables t = build_tables<NP>(sp, first ? nullptr : rev, smem_raw, groups);
   __syncthreads();
   uint32_t best = 0u;
-  for_each_allowed<true>(allowed, sp.total, [&](uint32_t i) {
-    int n2, o;
-    float d32;
-    double d64;
-    sum_groups<NP, true, false>(i, groups, t, n2, o, d32, d64);
-    if (o != 0) return false;  // not orthogonal to the row chosen last: rejected for good
-    const uint32_t key = order_key32(d32 * t.inv32[n2]);
+  visit_allowed<NP, true, true>(allowed, sp, groups, t, [&](const Cand<NP>& c) {
+    if (c.o != 0) return false;  // not orthogonal to the row chosen last: rejected for good
+    const uint32_t key = order_key32(c.d32 * t.inv32[c.n2]);
     best = key > best ? key : best;
     return true;
   });
@@ -261,9 +304,12 @@ __global__ void __launch_bounds__(256) search_max32(SearchParams sp, SearchState
   }
 }
 
+// FP64 maximum over the screened candidates; each is also written to the
+// hit list (while it has room) so that the pick pass can skip the scan.
 template <int NP>
 __global__ void __launch_bounds__(256) search_max64(SearchParams sp, SearchState* __restrict__ st,
-                                                    uint8_t* __restrict__ allowed) {
+                                                    uint8_t* __restrict__ allowed,
+                                                    SearchHit* __restrict__ hits) {
   if (st->dead || st->best32 == 0u) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int G = group_digits<NP>();
@@ -273,15 +319,13 @@ __global__ void __launch_bounds__(256) search_max64(SearchParams sp, SearchState
   __syncthreads();
   const float lim32 = key_value32(st->best32) - kScreen;
   unsigned long long best = 0ull;
-  for_each_allowed<false>(allowed, sp.total, [&](uint32_t i) {
-    int n2, o;
-    float d32;
-    double d64;
-    sum_groups<NP, false, false>(i, groups, t, n2, o, d32, d64);
-    if (d32 * t.inv32[n2] >= lim32) {
-      sum_groups<NP, false, true>(i, groups, t, n2, o, d32, d64);
-      const unsigned long long key = order_key(d64 * t.inv64[n2]);
+  visit_allowed<NP, false, false>(allowed, sp, groups, t, [&](const Cand<NP>& c) {
+    if (c.d32 * t.inv32[c.n2] >= lim32) {
+      const double cosv = c.d64() * t.inv64[c.n2];
+      const unsigned long long key = order_key(cosv);
       best = key > best ? key : best;
+      const uint32_t slot = atomicAdd(&st->n_hits, 1u);
+      if (slot < (uint32_t)sp.hit_cap) hits[slot] = SearchHit{c.i, c.n2, cosv};
     }
     return true;
   });
@@ -298,34 +342,40 @@ __global__ void __launch_bounds__(256) search_max64(SearchParams sp, SearchState
   }
 }
 
+// Winner among the candidates within the tie tolerance of the FP64 maximum:
+// block 0 reads the hit list, or, when the list overflowed, every block
+// scans again with the same screen.
 template <int NP>
 __global__ void __launch_bounds__(256) search_pick(SearchParams sp, SearchState* __restrict__ st,
-                                                   uint8_t* __restrict__ allowed) {
+                                                   uint8_t* __restrict__ allowed,
+                                                   const SearchHit* __restrict__ hits) {
   if (st->dead || st->best_key == 0ull) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int G = group_digits<NP>();
-  const int groups = (sp.N + G - 1) / G;
-  const Tables t = build_tables<NP>(sp, nullptr, smem_raw, groups);
-  __syncthreads();
-  const float lim32 = key_value32(st->best32) - kScreen;
+  const uint32_t n_hits = st->n_hits;
+  const bool from_list = n_hits <= (uint32_t)sp.hit_cap;
+  if (from_list && blockIdx.x != 0) return;
   const double lim64 = key_value(st->best_key) - kSearchTieTol;
   unsigned long long pick = ~0ull;
-  for_each_allowed<false>(allowed, sp.total, [&](uint32_t i) {
-    int n2, o;
-    float d32;
-    double d64;
-    sum_groups<NP, false, false>(i, groups, t, n2, o, d32, d64);
-    if (d32 * t.inv32[n2] >= lim32) {
-      sum_groups<NP, false, true>(i, groups, t, n2, o, d32, d64);
-      if (d64 * t.inv64[n2] >= lim64) {
-        const unsigned long long nk = sp.tie_large ? (unsigned long long)(0xffffff - n2)
-                                                   : (unsigned long long)n2;
-        const unsigned long long key = (nk << 32) | i;
-        pick = key < pick ? key : pick;
-      }
-    }
-    return true;
-  });
+  auto consider = [&](uint32_t i, int n2) {
+    const unsigned long long nk = sp.tie_large ? (unsigned long long)(0xffffff - n2)
+                                               : (unsigned long long)n2;
+    const unsigned long long key = (nk << 32) | i;
+    pick = key < pick ? key : pick;
+  };
+  if (from_list) {
+    for (uint32_t h = threadIdx.x; h < n_hits; h += blockDim.x)
+      if (hits[h].cosv >= lim64) consider(hits[h].i, hits[h].n2);
+  } else {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int G = group_digits<NP>();
+    const int groups = (sp.N + G - 1) / G;
+    const Tables t = build_tables<NP>(sp, nullptr, smem_raw, groups);
+    __syncthreads();
+    const float lim32 = key_value32(st->best32) - kScreen;
+    visit_allowed<NP, false, false>(allowed, sp, groups, t, [&](const Cand<NP>& c) {
+      if (c.d32 * t.inv32[c.n2] >= lim32 && c.d64() * t.inv64[c.n2] >= lim64) consider(c.i, c.n2);
+      return true;
+    });
+  }
   for (int off = 16; off > 0; off >>= 1) {
     const unsigned long long other = __shfl_down_sync(0xffffffffu, pick, off);
     pick = other < pick ? other : pick;
@@ -351,6 +401,7 @@ __global__ void search_commit(SearchParams sp, SearchState* __restrict__ st, int
   st->best32 = 0u;
   st->best_key = 0ull;
   st->pick_key = ~0ull;
+  st->n_hits = 0u;
 }
 
 constexpr int kSearchMaxSmem = 200 * 1024;
@@ -363,8 +414,8 @@ size_t table_bytes(const SearchParams& sp) {
 }
 
 template <int NP>
-cudaError_t enqueue_row(const SearchParams& sp, SearchState* st, uint8_t* allowed, int first,
-                        int slot, int grid, cudaStream_t s) {
+cudaError_t enqueue_row(const SearchParams& sp, SearchState* st, uint8_t* allowed, SearchHit* hits,
+                        int first, int slot, int grid, cudaStream_t s) {
   const size_t smem = table_bytes<NP>(sp);
   if (smem > (size_t)kSearchMaxSmem) return cudaErrorInvalidValue;
   // the opt-in shared-memory limit is raised once per instantiation
@@ -383,8 +434,8 @@ cudaError_t enqueue_row(const SearchParams& sp, SearchState* st, uint8_t* allowe
     for (int f = 0; f < sp.n_fixed; ++f) search_filter<NP><<<grid, 256, smem, s>>>(sp, allowed, f, 0);
   }
   search_max32<NP><<<grid, 256, smem, s>>>(sp, st, allowed, first);
-  search_max64<NP><<<grid, 256, smem, s>>>(sp, st, allowed);
-  search_pick<NP><<<grid, 256, smem, s>>>(sp, st, allowed);
+  search_max64<NP><<<grid, 256, smem, s>>>(sp, st, allowed, hits);
+  search_pick<NP><<<grid, 256, smem, s>>>(sp, st, allowed, hits);
   search_commit<NP><<<1, 1, 0, s>>>(sp, st, slot);
   return cudaGetLastError();
 }
@@ -392,7 +443,7 @@ cudaError_t enqueue_row(const SearchParams& sp, SearchState* st, uint8_t* allowe
 }  // namespace
 
 cudaError_t enqueue_search_row(const SearchParams& sp, SearchState* st, uint8_t* allowed,
-                               int first, int slot, cudaStream_t s) {
+                               SearchHit* hits, int first, int slot, cudaStream_t s) {
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -400,14 +451,14 @@ cudaError_t enqueue_search_row(const SearchParams& sp, SearchState* st, uint8_t*
   if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
   if (grid < 1) grid = 1;
   switch (sp.np) {
-    case 2: return enqueue_row<2>(sp, st, allowed, first, slot, (int)grid, s);
-    case 3: return enqueue_row<3>(sp, st, allowed, first, slot, (int)grid, s);
-    case 4: return enqueue_row<4>(sp, st, allowed, first, slot, (int)grid, s);
-    case 5: return enqueue_row<5>(sp, st, allowed, first, slot, (int)grid, s);
-    case 6: return enqueue_row<6>(sp, st, allowed, first, slot, (int)grid, s);
-    case 7: return enqueue_row<7>(sp, st, allowed, first, slot, (int)grid, s);
-    case 8: return enqueue_row<8>(sp, st, allowed, first, slot, (int)grid, s);
-    case 9: return enqueue_row<9>(sp, st, allowed, first, slot, (int)grid, s);
+    case 2: return enqueue_row<2>(sp, st, allowed, hits, first, slot, (int)grid, s);
+    case 3: return enqueue_row<3>(sp, st, allowed, hits, first, slot, (int)grid, s);
+    case 4: return enqueue_row<4>(sp, st, allowed, hits, first, slot, (int)grid, s);
+    case 5: return enqueue_row<5>(sp, st, allowed, hits, first, slot, (int)grid, s);
+    case 6: return enqueue_row<6>(sp, st, allowed, hits, first, slot, (int)grid, s);
+    case 7: return enqueue_row<7>(sp, st, allowed, hits, first, slot, (int)grid, s);
+    case 8: return enqueue_row<8>(sp, st, allowed, hits, first, slot, (int)grid, s);
+    case 9: return enqueue_row<9>(sp, st, allowed, hits, first, slot, (int)grid, s);
     default: return cudaErrorInvalidValue;
   }
 }

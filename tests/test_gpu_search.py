@@ -53,3 +53,25 @@ def test_search_N16_P1():
     if complete:
         gram = G @ G.T
         assert np.count_nonzero(gram - np.diag(np.diag(gram))) == 0
+
+
+@pytest.mark.parametrize("cap", [0, 1, 3])
+@pytest.mark.parametrize("tie", ["small", "large"])
+def test_search_hit_list_overflow_rescans(cap, tie):
+    """A row whose screened candidates overflow the hit list is decided by a
+    second full scan; with tiny capacities (D2 has many exact ties: scaled
+    copies of a vector) every such row takes that path, and the results still
+    match the oracle."""
+    want = dict(S.search_all_orders(S.P2, tie))
+    orders = list(want)[::37]
+    try:
+        P.tdct_debug_search_hit_cap(cap)
+        for order in orders:
+            got, complete = P.tdct_search(8, S.P2, [o - 1 for o in order], FIXED, tie)
+            T = want[order]
+            if T is None:
+                assert not complete, order
+            else:
+                assert complete and np.array_equal(np.array(got), T), order
+    finally:
+        P.tdct_debug_search_hit_cap(-1)
