@@ -283,7 +283,6 @@ __device__ __forceinline__ void load_block(const PlaneDesc& P, int by, int bx, b
 template <int R, int DT>
 __device__ __forceinline__ uint32_t codec_one(const PlaneDesc& P, int by, int bx,
                                               const RowWords<DT>& rw, const CodecParams& cp) {
-  constexpr int SB = DT == 0 ? 1 : 2;
   int32_t out[64];
   {
     uint32_t x[64];
