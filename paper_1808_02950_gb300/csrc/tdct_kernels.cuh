@@ -390,10 +390,12 @@ __device__ __forceinline__ uint2 round_pack_row_u8(const uint32_t n2[8]) {
 // which keeps 16 registers per block free between the forward and the
 // epilogue.
 struct RowsInRegs {
+  static constexpr bool kInSmem = false;
   const uint2* x;
   __device__ __forceinline__ uint2 row(int k) const { return x[k]; }
 };
 struct RowsInSmem {
+  static constexpr bool kInSmem = true;
   const uint8_t* p;
   __device__ __forceinline__ uint2 row(int k) const {
     return *reinterpret_cast<const uint2*>(p + k * 512);
@@ -484,20 +486,31 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8(const uint32_t w[64], XS
 // the kept rows.  The dense second pass then has kept_rows(R) inputs instead
 // of kept_cols(R); it yields columns, so the rounded samples are packed per
 // column pair and the row bytes assembled after columns 0-3 and 4-7.  It
-// holds more values live than the row-streaming order, so it is used only
-// where it removes a dense 8-input pass (policy 1, measured): kept set
-// spanning all 8 columns but not all 8 rows.  Policy 0: never; 2: whenever
-// kept_rows(R) < kept_cols(R).
+// holds more values live than the row-streaming order.  Policy 4 (default)
+// is the per-class choice measured on GB300 for the bulk-copy ring kernel
+// (samples re-read from shared memory; bench workload): rows first for
+// r-classes 6, 15, 16, 28 and 32 (1-3 % faster there), columns first for the
+// others (up to 1 % slower rows first).  Kernels that keep the samples in
+// registers use policy 1 (more values live would spill).  Policy 0: never;
+// 1: kept set spanning all 8 columns but not all 8 rows; 2: kept_rows(R) <
+// kept_cols(R); 3: kept_rows(R) <= kept_cols(R).
 #ifndef TDCT_INV_ROWS_FIRST
-#define TDCT_INV_ROWS_FIRST 1
+#define TDCT_INV_ROWS_FIRST 4
 #endif
 
-template <int R>
+template <int R, int POLICY>
+__host__ __device__ constexpr bool inverse_rows_first_policy() {
+  return POLICY == 4   ? (R == 6 || R == 15 || R == 16 || R == 28 || R == 32)
+         : POLICY == 3 ? kept_rows(R) <= kept_cols(R)
+         : POLICY == 2 ? kept_rows(R) < kept_cols(R)
+         : POLICY == 1 ? (kept_cols(R) == 8 && kept_rows(R) < 8)
+                       : false;
+}
+
+template <int R, typename XS>
 __host__ __device__ constexpr bool inverse_rows_first() {
-  return TDCT_INV_ROWS_FIRST == 3   ? kept_rows(R) <= kept_cols(R)
-         : TDCT_INV_ROWS_FIRST == 2 ? kept_rows(R) < kept_cols(R)
-         : TDCT_INV_ROWS_FIRST == 1 ? (kept_cols(R) == 8 && kept_rows(R) < 8)
-                                    : false;
+  return inverse_rows_first_policy<R, (TDCT_INV_ROWS_FIRST == 4 && !XS::kInSmem)
+                                          ? 1 : TDCT_INV_ROWS_FIRST>();
 }
 
 template <int R, typename XS>
@@ -557,14 +570,14 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8_rows(const uint32_t w[64
   return acc;
 }
 
-// Inverse pass order for class R (inverse_rows_first).
+// Inverse pass order for class R and sample source XS (inverse_rows_first).
 template <int R, typename XS>
 __device__ __forceinline__ uint32_t inverse_epilogue_u8_any(const uint32_t w[64], XS x,
                                                             uint2* __restrict__ out_row0,
                                                             int64_t out_pitch, bool store,
                                                             bool full, int valid_rows,
                                                             int valid_cols) {
-  if constexpr (inverse_rows_first<R>())
+  if constexpr (inverse_rows_first<R, XS>())
     return inverse_epilogue_u8_rows<R, XS>(w, x, out_row0, out_pitch, store, full, valid_rows,
                                        valid_cols);
   else
