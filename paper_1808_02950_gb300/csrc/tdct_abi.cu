@@ -1240,13 +1240,17 @@ int tdct_codec_error_jam(const void* d_img, int64_t pitch, int H, int W, int dty
   for (int i = 0; i < B; ++i) jp.q[i] = (int32_t)(L / n[i]);
   jp.L2 = L * L;
   jp.limit = 256 * 2 * jp.L2;
+  jp.hiw = (int32_t)(128 * 2 * jp.L2);
   jp.r = r;
   const int64_t d = 2 * jp.L2;
   int k = 32;
   while (k < 62 && (((int64_t)1 << (k + 1)) + d - 1) / d < ((int64_t)1 << 32)) ++k;
   const int64_t magic = (((int64_t)1 << k) + d - 1) / d;
   const int64_t err = magic * d - ((int64_t)1 << k);
-  if (jp.limit >= ((int64_t)1 << 31) ||
+  // the 32-bit second inverse stage of 16x16 u8 blocks needs |2N + L^2| < 2^31
+  // with |2N| <= 256 B L^2 (centred samples, orthogonal projection)
+  if ((B == 16 && dtype == TDCT_U8 && 256 * (int64_t)B * jp.L2 + jp.L2 >= ((int64_t)1 << 31)) ||
+      jp.limit >= ((int64_t)1 << 31) ||
       (unsigned __int128)err * (unsigned __int128)jp.limit >= ((unsigned __int128)1 << k))
     return fail(TDCT_EUNSUPPORTED, "no exact 32-bit division constant for L = %lld", (long long)L);
   jp.magic = (uint32_t)magic;

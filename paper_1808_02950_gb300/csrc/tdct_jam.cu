@@ -11,15 +11,23 @@
 // half-size inverses, then x_m = u_m + w_m, x_(N-1-m) = u_m - w_m.
 //
 // Exactness: Z = T X T^T is formed in 32-bit integers (|Z| < 2^20); the
-// inverse N = T^T (M o Z o q q^T) T in 64-bit integers (|N| < 2^43 at
-// N = 32), with q = L / n, L = lcm(n); the factor 2 q_i and the bias L^2 make
-// the last stage yield 2N + L^2, and x' = floor((2N + L^2) / (2 L^2)) once
-// the value is inside the clamp window (a 32-bit multiply-high with a
-// host-checked constant).
+// inverse N = T^T (M o Z o q q^T) T with q = L / n, L = lcm(n); the factor
+// 2 q_i and the bias L^2 make the last stage yield 2N + L^2, and
+// x' = floor((2N + L^2) / (2 L^2)) once the value is inside the clamp window
+// (a 32-bit multiply-high with a host-checked constant).  u8 samples enter
+// centred (x - 128; the reconstruction is shifted back by the rounding
+// bias): the kept-coefficient reconstruction is an orthogonal projection,
+// so |x'_exact - 128| <= ||X - 128||_F <= 128 B and |2N| <= 256 B L^2.  For
+// 16x16 u8 blocks that is below 2.13e9 < 2^31 and the second inverse stage
+// runs in 32-bit integers (wrapping intermediates, exact result); for 32x32
+// blocks and int16 residuals it runs in 64-bit integers.
 //
 // Work: a lane owns one row of a block (two 16x16 blocks or one 32x32 block
 // per warp); rows are transformed in registers, columns after a transpose
-// through a padded shared-memory tile, and back.
+// through a padded shared-memory tile, and back.  Kernels are compiled per
+// kept-extent class KE (every kept position (i, j) has i, j < KE): the row
+// forward forms KE outputs, only the KE leading columns are transformed, and
+// the row inverse has KE inputs; the exact r is applied at run time.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -78,7 +86,7 @@ __device__ __forceinline__ void jam_inv(const V* y, V* x) {
 
 // Scan index of (i, j) in the B x B zig-zag (anti-diagonals; odd ones start
 // at (0, s) with i increasing, even ones at (s, 0) with i decreasing).
-__device__ __forceinline__ int zz_b(int B, int i, int j) {
+__host__ __device__ __forceinline__ int zz_b(int B, int i, int j) {
   const int s = i + j;
   if (s < B) return s * (s + 1) / 2 + ((s & 1) ? i : s - i);
   const int before = B * B - (2 * B - 1 - s) * (2 * B - s) / 2;
@@ -122,13 +130,17 @@ struct RowRaw {
 // stage and both transposes run in 32 bits, elsewhere in 64.
 template <int B, int DT>
 using StageA = std::conditional_t<(B == 16 || DT == 0), uint32_t, long long>;
-
+// The row inverse (second stage) in 32 bits: 16x16 u8 blocks (see above).
 template <int B, int DT>
+constexpr bool kStageB32 = (B == 16 && DT == 0);
+
+template <int B, int DT, int KE>
 __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const JamParams jp,
                                                         unsigned long long* __restrict__ sse_out) {
   constexpr int BPW = 32 / B;  // blocks per warp
   constexpr int SB = DT == 0 ? 1 : 2;
   using VA = StageA<B, DT>;
+  using VB = std::conditional_t<kStageB32<B, DT>, uint32_t, long long>;
   using TileT = std::conditional_t<std::is_same_v<VA, uint32_t>, int32_t, long long>;
   __shared__ TileT tile[4][BPW][B][B + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -138,6 +150,10 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   TileT (*tl)[B + 1] = tile[wid][bsub];
   const int hk = kept_height(B, jp.r, k);  // the lane's column in the column stage
+  // rounding bias folded into the DC input of the row inverse (T's first row
+  // is all ones, so it reaches every output): L^2, plus the centring shift
+  // 128 * 2 L^2 where the stage is 64-bit
+  const VB bias = DT == 0 ? (VB)(kStageB32<B, DT> ? jp.L2 : jp.L2 + jp.hiw) : (VB)0;
   unsigned long long acc = 0;
   for (int64_t base = warp * BPW; base < nb; base += nwarps * BPW) {
     const int64_t blk = base + bsub;
@@ -145,7 +161,8 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
     const int by = valid ? (int)(blk / nbx) : 0, bx = valid ? (int)(blk - (int64_t)by * nbx) : 0;
     const int y = by * B + k;
     const bool full = valid && (by + 1) * B <= P.H && (bx + 1) * B <= P.W;
-    // rows: t = T x for row k of the block; the raw row stays for the error
+    // rows: t = T x for row k of the block (KE leading outputs); the raw row
+    // stays for the error
     RowRaw<B, DT> raw;
     {
       if (full && (jp.aligned & 1)) {
@@ -168,14 +185,15 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
       }
       uint32_t x[B], t[B];
 #pragma unroll
-      for (int l = 0; l < B; ++l) x[l] = (uint32_t)raw.at(l);
+      for (int l = 0; l < B; ++l) x[l] = (uint32_t)(raw.at(l) - (DT == 0 ? 128 : 0));
       jam_fwd<B, uint32_t>(x, t);
 #pragma unroll
-      for (int j = 0; j < B; ++j) tl[k][j] = (TileT)(int32_t)t[j];
+      for (int j = 0; j < KE; ++j) tl[k][j] = (TileT)(int32_t)t[j];
     }
     __syncwarp();
-    // column c = k: Z[i][c], zonal mask with 2 q_i, inverse along the column
-    {
+    // column c = k < KE: Z[i][c] (i < KE), zonal mask with 2 q_i, inverse
+    // along the column; a lane reads and writes its own column only
+    if (k < KE) {
       uint32_t col[B], z[B];
 #pragma unroll
       for (int i = 0; i < B; ++i) col[i] = (uint32_t)tl[i][k];
@@ -183,19 +201,21 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
       VA w[B], u[B];
 #pragma unroll
       for (int i = 0; i < B; ++i)
-        w[i] = i < hk ? (VA)((long long)(int32_t)z[i] * (2 * jp.q[i])) : (VA)0;
+        w[i] = (i < KE && i < hk) ? (VA)((long long)(int32_t)z[i] * (2 * jp.q[i])) : (VA)0;
       jam_inv<B, VA>(w, u);
-      __syncwarp();
 #pragma unroll
       for (int i = 0; i < B; ++i) tl[i][k] = (TileT)u[i];
     }
     __syncwarp();
-    // row k: 2N[k][l] = sum_j q_j V'[k][j] T[j][l]; round, clamp, error, store
+    // row k: 2N[k][l] + bias = sum_j q_j V'[k][j] T[j][l] (j < KE); round,
+    // clamp, error, store
     {
-      long long v[B], n2[B];
+      VB v[B], n2[B];
 #pragma unroll
-      for (int j = 0; j < B; ++j) v[j] = (long long)tl[k][j] * jp.q[j];
-      jam_inv<B, long long>(v, n2);
+      for (int j = 0; j < B; ++j)
+        v[j] = j < KE ? (VB)tl[k][j] * (VB)jp.q[j] : (VB)0;
+      v[0] += bias;
+      jam_inv<B, VB>(v, n2);
       RowRaw<B, DT> out;
       uint32_t* ou = reinterpret_cast<uint32_t*>(out.w);
 #pragma unroll
@@ -205,16 +225,26 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
 #pragma unroll
       for (int l = 0; l < B; ++l) {
         int32_t xr;
-        if (DT == 0) {
-          const long long a = n2[l] + jp.L2;
-          xr = a < 0 ? 0 : (a >= jp.limit ? 255 : (int32_t)(__umulhi((uint32_t)a, jp.magic) >> jp.shift));
-          xr = min(xr, 255);
+        if constexpr (DT == 0) {
+          if constexpr (kStageB32<B, DT>) {
+            // n2 = 2N + L^2 exactly; shift by 128 * 2 L^2 after capping so the
+            // sum cannot wrap; values above the window reach 256 -> 255
+            const int32_t a = min((int32_t)n2[l], jp.hiw) + jp.hiw;
+            xr = a < 0 ? 0 : min((int32_t)(__umulhi((uint32_t)a, jp.magic) >> jp.shift), 255);
+          } else {
+            const long long a = (long long)n2[l];  // 2N + L^2 + 128 * 2 L^2
+            xr = a < 0 ? 0
+                       : (a >= jp.limit ? 255
+                                        : min((int32_t)(__umulhi((uint32_t)a, jp.magic) >> jp.shift),
+                                              255));
+          }
           ou[l >> 2] |= (uint32_t)xr << (8 * (l & 3));
         } else {
-          const long long a = (n2[l] < 0 ? -n2[l] : n2[l]) + jp.L2;
+          const long long nn = (long long)n2[l];
+          const long long a = (nn < 0 ? -nn : nn) + jp.L2;
           int32_t m = a >= jp.limit ? 255 : (int32_t)(__umulhi((uint32_t)a, jp.magic) >> jp.shift);
           m = min(m, 255);
-          xr = n2[l] < 0 ? -m : m;
+          xr = nn < 0 ? -m : m;
           ou[l >> 1] |= ((uint32_t)xr & 0xffffu) << (16 * (l & 1));
         }
         const bool in = full || (row_in && bx * B + l < P.W);
@@ -244,7 +274,14 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   if (lane == 0 && acc) atomicAdd(sse_out, acc);
 }
 
-template <int B, int DT>
+// Kept-extent classes: the smallest class at least the extent of the first
+// r zig-zag positions of a B x B block.
+__host__ __device__ constexpr int jam_extent_class(int ext) {
+  return ext <= 2 ? 2 : ext <= 4 ? 4 : ext <= 6 ? 6 : ext <= 8 ? 8 : ext <= 12 ? 12
+       : ext <= 16 ? 16 : ext <= 24 ? 24 : 32;
+}
+
+template <int B, int DT, int KE>
 cudaError_t launch_b(const PlaneDesc& P, const JamParams& jp, unsigned long long* sse,
                      cudaStream_t s) {
   int dev = 0, sms = 148;
@@ -255,16 +292,43 @@ cudaError_t launch_b(const PlaneDesc& P, const JamParams& jp, unsigned long long
   int64_t grid = (warps + 3) / 4;
   if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
   if (grid < 1) grid = 1;
-  jam_codec_kernel<B, DT><<<(unsigned)grid, 128, 0, s>>>(P, jp, sse);
+  jam_codec_kernel<B, DT, KE><<<(unsigned)grid, 128, 0, s>>>(P, jp, sse);
   return cudaGetLastError();
+}
+
+template <int B, int DT>
+cudaError_t launch_ke(int ke, const PlaneDesc& P, const JamParams& jp, unsigned long long* sse,
+                      cudaStream_t s) {
+  switch (ke) {
+    case 2: return launch_b<B, DT, 2>(P, jp, sse, s);
+    case 4: return launch_b<B, DT, 4>(P, jp, sse, s);
+    case 6: return launch_b<B, DT, 6>(P, jp, sse, s);
+    case 8: return launch_b<B, DT, 8>(P, jp, sse, s);
+    case 12: return launch_b<B, DT, 12>(P, jp, sse, s);
+    case 16: return launch_b<B, DT, 16>(P, jp, sse, s);
+    default:
+      if constexpr (B == 32) {
+        if (ke == 24) return launch_b<B, DT, 24>(P, jp, sse, s);
+        if (ke == 32) return launch_b<B, DT, 32>(P, jp, sse, s);
+      }
+      return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_jam_codec(int B, const PlaneDesc& P, const JamParams& jp,
                              unsigned long long* sse, cudaStream_t s) {
-  if (B == 16) return P.dtype == 0 ? launch_b<16, 0>(P, jp, sse, s) : launch_b<16, 1>(P, jp, sse, s);
-  if (B == 32) return P.dtype == 0 ? launch_b<32, 0>(P, jp, sse, s) : launch_b<32, 1>(P, jp, sse, s);
+  // extent of the first r scan positions: 1 + the largest row or column index
+  int ext = 0;
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j)
+      if (zz_b(B, i, j) < jp.r) ext = max(ext, max(i, j) + 1);
+  const int ke = min(jam_extent_class(ext), B);
+  if (B == 16)
+    return P.dtype == 0 ? launch_ke<16, 0>(ke, P, jp, sse, s) : launch_ke<16, 1>(ke, P, jp, sse, s);
+  if (B == 32)
+    return P.dtype == 0 ? launch_ke<32, 0>(ke, P, jp, sse, s) : launch_ke<32, 1>(ke, P, jp, sse, s);
   return cudaErrorInvalidValue;
 }
 

@@ -13,6 +13,7 @@ struct JamParams {
   int32_t q[32];     // q_i = L / n_i
   long long L2;      // L^2 (the rounding bias of the doubled inverse)
   long long limit;   // 256 * 2 L^2: values at or above clamp to 255
+  int32_t hiw;       // 128 * 2 L^2: the centring shift of u8 samples
   uint32_t magic;    // floor(a / (2 L^2)) == umulhi(a, magic) >> shift for 0 <= a < limit
   int32_t shift;
   int32_t r;         // retained coefficients, 1..B^2

@@ -969,12 +969,20 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
   }
 }
 
-// Slots per warp of the bulk-copy ring (3 CTAs x 4 warps x 4 x 4 KB = 192 KB
-// per SM); a slot is refilled after its unit is done, so 3 units stay in
-// flight while one is computed.
-#ifndef TDCT_U8_STAGES
-#define TDCT_U8_STAGES 4
+// Slots per warp of the bulk-copy ring; a slot is refilled after its unit is
+// done, so STAGES - 1 units stay in flight while one is computed.  Measured
+// on GB300 (bench workload): 4 slots (3 CTAs x 4 warps x 4 x 4 KB = 192 KB
+// per SM) for the classes up to 10, where the kernel runs near the memory
+// side's limit; 3 slots for classes 15 to 32 (0.5-1.6 % faster there, the
+// compute-bound range); 4 for the 2-CTA classes from 36.
+template <int R>
+__host__ __device__ constexpr int ring_stages() {
+#ifdef TDCT_U8_STAGES
+  return TDCT_U8_STAGES;
+#else
+  return (R >= 15 && R <= 32) ? 3 : 4;
 #endif
+}
 
 inline int device_sms() {
   int dev = 0, sms = 0;
@@ -990,7 +998,7 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
                          int max_ctas, cudaStream_t s) {
   constexpr int kThreads = 256;
   constexpr int kRingThreads = TDCT_RING_THREADS;
-  constexpr int kStages = TDCT_U8_STAGES;
+  constexpr int kStages = ring_stages<R>();
   constexpr size_t kSmem = (size_t)(kRingThreads / 32) * kStages * (kUnitBytes + 8);
   static int resident = 0, resident_bulk = 0;  // CTAs per SM, computed once
   static int sms = 0;

@@ -32,7 +32,8 @@ def test_jam_codec_matches_oracle(B, T, dtype, H, W):
         host = rng.integers(0, 256, (H, W)).astype(np.uint8)
     else:
         host = rng.integers(-255, 256, (H, W)).astype(np.int16)
-    for r in (1, 3, 10, 50, 136, B * B // 2, B * B):
+    # kept-extent classes 2, 2, 4, 6, 8, 12, 16, 16 (B = 16) or 24, 32, 32 (B = 32)
+    for r in (1, 3, 10, 16, 28, 50, 136, 300 if B == 32 else 200, B * B // 2, B * B):
         sse, rec, psnr = run(host, B, T, r)
         want_sse, want_rec = oc.codec_plane_b(host, T, B, r)
         assert np.array_equal(rec, want_rec), f"B={B} r={r}"
@@ -58,7 +59,7 @@ def test_jam_codec_smooth_image_and_extremes(B, T):
         s = np.sign(np.outer(T[i], T[(3 * i + 1) % B]))
         blocks.append(np.where(s > 0, 255, 0))
     ext = np.ascontiguousarray(np.concatenate([b.astype(np.uint8) for b in blocks], axis=1))
-    for r in (1, 5, B * B):
+    for r in (1, 5, 16, 136, B * B):
         sse, rec, _ = run(ext, B, T, r)
         want_sse, want_rec = oc.codec_plane_b(ext, T, B, r)
         assert sse == want_sse and np.array_equal(rec, want_rec)
