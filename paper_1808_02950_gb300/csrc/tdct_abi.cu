@@ -1255,6 +1255,18 @@ int tdct_codec_error_jam(const void* d_img, int64_t pitch, int H, int W, int dty
     return fail(TDCT_EUNSUPPORTED, "no exact 32-bit division constant for L = %lld", (long long)L);
   jp.magic = (uint32_t)magic;
   jp.shift = k - 32;
+  {
+    // the 16x16 u8 epilogue: x' in the upper half of a signed 32-bit high
+    // product, exact for 0 <= a <= limit (and negative for negative a)
+    const int64_t m16 = (((int64_t)1 << 48) + d - 1) / d;
+    const int64_t err16 = m16 * d - ((int64_t)1 << 48);
+    if (B == 16 && dtype == TDCT_U8 &&
+        (m16 >= ((int64_t)1 << 31) ||
+         (unsigned __int128)err16 * (unsigned __int128)(jp.limit + 1) >= ((unsigned __int128)1 << 48)))
+      return fail(TDCT_EUNSUPPORTED, "no exact 16-bit-lane division constant for L = %lld",
+                  (long long)L);
+    jp.magic16 = (int32_t)m16;
+  }
   const auto a16 = [](const void* p, int64_t pitch) {
     return ((reinterpret_cast<uintptr_t>(p) | (uintptr_t)pitch) & 15) == 0;
   };

@@ -222,16 +222,45 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
       for (int q = 0; q < 4 * RowRaw<B, DT>::kWords; ++q) ou[q] = 0u;
       uint32_t sse = 0;
       const bool row_in = valid && y < P.H;
+      if constexpr (kStageB32<B, DT>) {
+        // n2 = 2N + L^2 exactly; capped at 128 * 2 L^2 and shifted by it (no
+        // wrap), the signed high product with magic16 carries
+        // floor(a / (2 L^2)) = x' in its upper 16 bits (negative below the
+        // window); pairs are clamped to [0, 255] as s16x2 and packed to bytes
+        uint32_t h[B];
+#pragma unroll
+        for (int l = 0; l < B; ++l) {
+          const int32_t a = min((int32_t)n2[l], jp.hiw) + jp.hiw;
+          h[l] = (uint32_t)__mulhi(a, jp.magic16);
+        }
+#pragma unroll
+        for (int q = 0; q < B / 4; ++q) {
+          const uint32_t c01 = min_relu_s16x2(__byte_perm(h[4 * q], h[4 * q + 1], 0x7632u), 0x00ff00ffu);
+          const uint32_t c23 =
+              min_relu_s16x2(__byte_perm(h[4 * q + 2], h[4 * q + 3], 0x7632u), 0x00ff00ffu);
+          ou[q] = __byte_perm(c01, c23, 0x6420u);
+        }
+        const uint32_t* ru = reinterpret_cast<const uint32_t*>(raw.w);
+        if (full) {
+#pragma unroll
+          for (int q = 0; q < B / 4; ++q) {
+            const uint32_t dq = __vabsdiffu4(ru[q], ou[q]);
+            sse = __dp4a(dq, dq, sse);
+          }
+        } else {
+#pragma unroll
+          for (int l = 0; l < B; ++l) {
+            const bool in = row_in && bx * B + l < P.W;
+            const int32_t d = raw.at(l) - out.at(l);
+            sse += in ? (uint32_t)(d * d) : 0u;
+          }
+        }
+      } else {
 #pragma unroll
       for (int l = 0; l < B; ++l) {
         int32_t xr;
         if constexpr (DT == 0) {
-          if constexpr (kStageB32<B, DT>) {
-            // n2 = 2N + L^2 exactly; shift by 128 * 2 L^2 after capping so the
-            // sum cannot wrap; values above the window reach 256 -> 255
-            const int32_t a = min((int32_t)n2[l], jp.hiw) + jp.hiw;
-            xr = a < 0 ? 0 : min((int32_t)(__umulhi((uint32_t)a, jp.magic) >> jp.shift), 255);
-          } else {
+          {
             const long long a = (long long)n2[l];  // 2N + L^2 + 128 * 2 L^2
             xr = a < 0 ? 0
                        : (a >= jp.limit ? 255
@@ -250,6 +279,7 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
         const bool in = full || (row_in && bx * B + l < P.W);
         const int32_t d = raw.at(l) - xr;
         sse += in ? (uint32_t)(d * d) : 0u;
+      }
       }
       acc += sse;
       if (P.recon && row_in) {

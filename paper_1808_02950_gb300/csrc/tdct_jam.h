@@ -16,6 +16,7 @@ struct JamParams {
   int32_t hiw;       // 128 * 2 L^2: the centring shift of u8 samples
   uint32_t magic;    // floor(a / (2 L^2)) == umulhi(a, magic) >> shift for 0 <= a < limit
   int32_t shift;
+  int32_t magic16;   // floor(a / (2 L^2)) == mulhi(a, magic16) >> 16 for 0 <= a <= limit
   int32_t r;         // retained coefficients, 1..B^2
   int32_t aligned;   // bit 0: image rows 16-byte aligned, bit 1: reconstruction rows
 };
