@@ -255,31 +255,49 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
             sse += in ? (uint32_t)(d * d) : 0u;
           }
         }
-      } else {
+      } else if constexpr (DT == 0) {
+        // 64-bit stage: n2 = 2N + L^2 + 128 * 2 L^2; clamped to [0, limit]
+        // before the 32-bit division (limit itself gives 256 -> 255)
+        uint32_t qv[B];
 #pragma unroll
-      for (int l = 0; l < B; ++l) {
-        int32_t xr;
-        if constexpr (DT == 0) {
-          {
-            const long long a = (long long)n2[l];  // 2N + L^2 + 128 * 2 L^2
-            xr = a < 0 ? 0
-                       : (a >= jp.limit ? 255
-                                        : min((int32_t)(__umulhi((uint32_t)a, jp.magic) >> jp.shift),
-                                              255));
+        for (int l = 0; l < B; ++l) {
+          const long long a = (long long)n2[l];
+          const uint32_t ac = a < 0 ? 0u : (a > jp.limit ? (uint32_t)jp.limit : (uint32_t)a);
+          qv[l] = min(__umulhi(ac, jp.magic) >> jp.shift, 255u);
+        }
+#pragma unroll
+        for (int q = 0; q < B / 4; ++q)
+          ou[q] = __byte_perm(__byte_perm(qv[4 * q], qv[4 * q + 1], 0x0040u),
+                              __byte_perm(qv[4 * q + 2], qv[4 * q + 3], 0x0040u), 0x5410u);
+        const uint32_t* ru = reinterpret_cast<const uint32_t*>(raw.w);
+        if (full) {
+#pragma unroll
+          for (int q = 0; q < B / 4; ++q) {
+            const uint32_t dq = __vabsdiffu4(ru[q], ou[q]);
+            sse = __dp4a(dq, dq, sse);
           }
-          ou[l >> 2] |= (uint32_t)xr << (8 * (l & 3));
         } else {
+#pragma unroll
+          for (int l = 0; l < B; ++l) {
+            const bool in = row_in && bx * B + l < P.W;
+            const int32_t d = raw.at(l) - out.at(l);
+            sse += in ? (uint32_t)(d * d) : 0u;
+          }
+        }
+      } else {
+        // int16 residuals: |x'| rounded half away from zero, clamped to 255
+#pragma unroll
+        for (int l = 0; l < B; ++l) {
           const long long nn = (long long)n2[l];
           const long long a = (nn < 0 ? -nn : nn) + jp.L2;
           int32_t m = a >= jp.limit ? 255 : (int32_t)(__umulhi((uint32_t)a, jp.magic) >> jp.shift);
           m = min(m, 255);
-          xr = nn < 0 ? -m : m;
+          const int32_t xr = nn < 0 ? -m : m;
           ou[l >> 1] |= ((uint32_t)xr & 0xffffu) << (16 * (l & 1));
+          const bool in = full || (row_in && bx * B + l < P.W);
+          const int32_t d = raw.at(l) - xr;
+          sse += in ? (uint32_t)(d * d) : 0u;
         }
-        const bool in = full || (row_in && bx * B + l < P.W);
-        const int32_t d = raw.at(l) - xr;
-        sse += in ? (uint32_t)(d * d) : 0u;
-      }
       }
       acc += sse;
       if (P.recon && row_in) {
