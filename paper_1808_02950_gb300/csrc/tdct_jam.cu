@@ -149,7 +149,14 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   TileT (*tl)[B + 1] = tile[wid][bsub];
-  const int hk = kept_height(B, jp.r, k);  // the lane's column in the column stage
+  // the column stage: two lanes per column when the kept extent allows (16x16
+  // blocks; at 32x32 the extra registers cost a resident CTA and the split
+  // measured 2 % slower)
+  constexpr bool kSplit = B == 16 && 2 * KE <= B;
+  constexpr uint32_t kBlockMask = (2 * KE >= 32) ? 0xffffffffu : ((1u << (2 * KE)) - 1u);
+  constexpr uint32_t kSplitMask = B == 16 ? (kBlockMask | (kBlockMask << 16)) : kBlockMask;
+  // kept rows of the lane's column in the column stage
+  const int hk = kept_height(B, jp.r, kSplit ? (k >> 1) : k);
   // rounding bias folded into the DC input of the row inverse (T's first row
   // is all ones, so it reaches every output): L^2, plus the centring shift
   // 128 * 2 L^2 where the stage is 64-bit
@@ -191,9 +198,41 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
       for (int j = 0; j < KE; ++j) tl[k][j] = (TileT)(int32_t)t[j];
     }
     __syncwarp();
-    // column c = k < KE: Z[i][c] (i < KE), zonal mask with 2 q_i, inverse
-    // along the column; a lane reads and writes its own column only
-    if (k < KE) {
+    // columns c < KE: Z[i][c] (i < KE), zonal mask with 2 q_i, inverse along
+    // the column.  With 2 KE <= B = 16 two lanes share a column: lane half h takes
+    // the sums (h = 0: even rows of Z) or the differences (h = 1: odd rows)
+    // of the first JAM stage, the half-size forward and inverse, and the
+    // pair combines u +- w by one exchange; otherwise one lane per column.
+    // Lanes write only the column they read.
+    if constexpr (kSplit) {
+      if (k < 2 * KE) {
+        const int c = k >> 1;
+        const uint32_t hm = (k & 1) ? 0xffffffffu : 0u;  // all ones for h = 1
+        uint32_t col[B], v[B / 2], zh[B / 2];
+#pragma unroll
+        for (int i = 0; i < B; ++i) col[i] = (uint32_t)tl[i][c];
+#pragma unroll
+        for (int m = 0; m < B / 2; ++m) v[m] = col[m] + (col[B - 1 - m] ^ hm) - hm;
+        jam_fwd<B / 2, uint32_t>(v, zh);  // zh[i] = Z[2 i + h][c]
+        VA w[B / 2], rh[B / 2];
+#pragma unroll
+        for (int i = 0; i < B / 2; ++i) {
+          const int ifull = 2 * i + (int)(hm & 1u);
+          const int32_t qm = hm ? jp.q[2 * i + 1] : jp.q[2 * i];
+          w[i] = (2 * i < KE && ifull < KE && ifull < hk)
+                     ? (VA)((long long)(int32_t)zh[i] * (2 * qm)) : (VA)0;
+        }
+        jam_inv<B / 2, VA>(w, rh);  // h = 0: u, h = 1: w
+        const int rx = hm ? B - 1 : 0;
+#pragma unroll
+        for (int m = 0; m < B / 2; ++m) {
+          const VA pm = __shfl_xor_sync(kSplitMask, rh[m], 1);
+          // h = 0: row m = u + w; h = 1: row B - 1 - m = u - w
+          const VA val = hm ? pm - rh[m] : rh[m] + pm;
+          tl[m ^ rx][c] = (TileT)val;
+        }
+      }
+    } else if (k < KE) {
       uint32_t col[B], z[B];
 #pragma unroll
       for (int i = 0; i < B; ++i) col[i] = (uint32_t)tl[i][k];
