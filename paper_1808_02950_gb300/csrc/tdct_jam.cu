@@ -162,34 +162,79 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   // 128 * 2 L^2 where the stage is 64-bit
   const VB bias = DT == 0 ? (VB)(kStageB32<B, DT> ? jp.L2 : jp.L2 + jp.hiw) : (VB)0;
   unsigned long long acc = 0;
-  for (int64_t base = warp * BPW; base < nb; base += nwarps * BPW) {
-    const int64_t blk = base + bsub;
-    const bool valid = blk < nb;
-    const int by = valid ? (int)(blk / nbx) : 0, bx = valid ? (int)(blk - (int64_t)by * nbx) : 0;
-    const int y = by * B + k;
-    const bool full = valid && (by + 1) * B <= P.H && (bx + 1) * B <= P.W;
-    // rows: t = T x for row k of the block (KE leading outputs); the raw row
-    // stays for the error
-    RowRaw<B, DT> raw;
-    {
-      if (full && (jp.aligned & 1)) {
-        const uint4* src =
-            reinterpret_cast<const uint4*>(P.img + (int64_t)y * P.pitch + (int64_t)bx * B * SB);
+  // Block geometry of the lane at warp position b (one division; 32-bit when
+  // the plane's block count allows).
+  struct Geo {
+    bool valid, full;
+    int by, bx;
+  };
+  const bool small = nb < ((int64_t)1 << 31);
+  auto geo_of = [&](int64_t b) {
+    Geo g;
+    const int64_t blk = b + bsub;
+    g.valid = blk < nb;
+    if (small) {
+      const int q = (int)blk / (int)nbx;
+      g.by = g.valid ? q : 0;
+      g.bx = g.valid ? (int)blk - q * (int)nbx : 0;
+    } else {
+      g.by = g.valid ? (int)(blk / nbx) : 0;
+      g.bx = g.valid ? (int)(blk - (int64_t)g.by * nbx) : 0;
+    }
+    g.full = g.valid && (g.by + 1) * B <= P.H && (g.bx + 1) * B <= P.W;
+    return g;
+  };
+  // The lane's row k of the block at g (zero outside the plane).
+  auto fetch_row = [&](const Geo& g, RowRaw<B, DT>& rr) {
+    const int fy = g.by * B + k;
+    if (g.full && (jp.aligned & 1)) {
+      const uint4* src =
+          reinterpret_cast<const uint4*>(P.img + (int64_t)fy * P.pitch + (int64_t)g.bx * B * SB);
 #pragma unroll
-        for (int q = 0; q < RowRaw<B, DT>::kWords; ++q) raw.w[q] = __ldg(src + q);
-      } else {
-        uint32_t* u = reinterpret_cast<uint32_t*>(raw.w);
+      for (int q = 0; q < RowRaw<B, DT>::kWords; ++q) rr.w[q] = __ldg(src + q);
+    } else {
+      uint32_t* u = reinterpret_cast<uint32_t*>(rr.w);
 #pragma unroll
-        for (int q = 0; q < 4 * RowRaw<B, DT>::kWords; ++q) u[q] = 0u;
-        if (valid) {
+      for (int q = 0; q < 4 * RowRaw<B, DT>::kWords; ++q) u[q] = 0u;
+      if (g.valid) {
 #pragma unroll
-          for (int l = 0; l < B; ++l) {
-            const uint32_t v = (uint32_t)load_px<DT>(P, y, bx * B + l);
-            if (DT == 0) u[l >> 2] |= (v & 0xffu) << (8 * (l & 3));
-            else u[l >> 1] |= (v & 0xffffu) << (16 * (l & 1));
-          }
+        for (int l = 0; l < B; ++l) {
+          const uint32_t v = (uint32_t)load_px<DT>(P, fy, g.bx * B + l);
+          if (DT == 0) u[l >> 2] |= (v & 0xffu) << (8 * (l & 3));
+          else u[l >> 1] |= (v & 0xffffu) << (16 * (l & 1));
         }
       }
+    }
+  };
+  // 32x32 blocks fetch their rows one iteration ahead (the loads of the next
+  // block are in flight while the current one is transformed: 5 % faster);
+  // 16x16 blocks fetch right before use (prefetching measured 2 % slower)
+  constexpr bool kPrefetch = B == 32;
+  RowRaw<B, DT> raw_next;
+  Geo g_next{};
+  if (kPrefetch && warp * BPW < nb) {
+    g_next = geo_of(warp * BPW);
+    fetch_row(g_next, raw_next);
+  }
+  for (int64_t base = warp * BPW; base < nb; base += nwarps * BPW) {
+    Geo g;
+    RowRaw<B, DT> raw;  // the raw row stays for the error
+    if constexpr (kPrefetch) {
+      g = g_next;
+      raw = raw_next;
+      if (base + nwarps * BPW < nb) {
+        g_next = geo_of(base + nwarps * BPW);
+        fetch_row(g_next, raw_next);
+      }
+    } else {
+      g = geo_of(base);
+      fetch_row(g, raw);
+    }
+    const bool valid = g.valid, full = g.full;
+    const int by = g.by, bx = g.bx;
+    const int y = by * B + k;
+    // rows: t = T x for row k of the block (KE leading outputs)
+    {
       uint32_t x[B], t[B];
 #pragma unroll
       for (int l = 0; l < B; ++l) x[l] = (uint32_t)(raw.at(l) - (DT == 0 ? 128 : 0));
