@@ -162,23 +162,6 @@ struct CodecParams {
 };
 
 // Forward, zonal mask, scale by q_i q_j, inverse, round and clamp one block.
-// R is the launch's r-class: positions with scan index >= R are known to be
-// zero at compile time, so the work they would need is never emitted; the
-// exact r <= R is applied through cmul.  Returns the reconstruction in out[64].
-template <int R, int DT>
-__device__ __forceinline__ void codec_block(const uint32_t x[64], int32_t out[64],
-                                            const CodecParams& cp) {
-  uint32_t z[64];
-  fwd2d<uint32_t>(x, z);
-  uint32_t w[64];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      w[8 * i + j] = kept(R, i, j) ? z[8 * i + j] * (uint32_t)cp.cmul[8 * i + j] : 0u;
-  reconstruct<DT>(w, out);
-}
-
 __device__ __forceinline__ uint2 pack_u8x8(const int32_t* v) {
   uint2 w;
   w.x = (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16) | ((uint32_t)v[3] << 24);
@@ -279,51 +262,107 @@ __device__ __forceinline__ void load_block(const PlaneDesc& P, int by, int bx, b
   }
 }
 
-// Codec of one block held as raw row words; returns its SSE over valid samples.
-template <int R, int DT>
-__device__ __forceinline__ uint32_t codec_one(const PlaneDesc& P, int by, int bx,
-                                              const RowWords<DT>& rw, const CodecParams& cp) {
-  int32_t out[64];
+// ---- int16 residual path: one block at a time, epilogue streamed by rows ------
+//
+// Residuals reach |Z| = 36720 (> int16), so the forward is per block in int32.
+// The inverse uses the doubled multipliers (2N) and is streamed row by row
+// into rounding, SSE and the store, which keeps no 64-sample output array
+// live.  Rounding half away from zero for both signs:
+//   x' = floor((2N + L^2 - [N < 0]) / (2 L^2)),
+// evaluated as floor((2N + L^2 - [N < 0] + 2048 * 2 L^2) / (2 L^2)) - 2048 so
+// that the dividend stays in [2.2e6, 1.06e9] (|2N| <= 2 * 255 * 8 * L^2 by the
+// orthogonal-projection bound), where mulhi(a, kDivMagic) >> 16 is exact; the
+// offset quotient is clamped to 2048 +- 255.
+constexpr int32_t kI16Bias = (int32_t)(kL2 + 2048u * 2u * kL2);
+
+template <int R>
+__device__ __forceinline__ uint32_t codec_block_i16(const PlaneDesc& P, int by, int bx,
+                                                    const RowWords<1>& rw, const CodecParams& cp,
+                                                    int valid_rows, int valid_cols) {
+  const bool full = valid_rows == 8 && valid_cols == 8;
+  uint32_t w[64];
   {
-    uint32_t x[64];
+    uint32_t x[64], z[64];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) unpack_row<DT>(rw, k, x + 8 * k);
-    codec_block<R, DT>(x, out, cp);
+    for (int k = 0; k < 8; ++k) unpack_i16x8(rw.w[k], x + 8 * k);
+    fwd2d<uint32_t>(x, z);
+#pragma unroll
+    for (int p = 0; p < 64; ++p)
+      w[p] = kept(R, p / 8, p % 8) ? z[p] * (uint32_t)cp.cmul2[p] : 0u;
   }
-  const bool full = (by * 8 + 8 <= P.H) && ((bx + 1) * 8 <= P.W);
-  uint32_t sse = 0;
+  // columns first: v[k][j] = sum_i t_i[k] w[i][j]
+  uint32_t v[64];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    uint32_t col[8], o[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) col[i] = w[8 * i + j];
+    inv8<uint32_t>(col, o);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[8 * k + j] = o[k];
+  }
+  const bool store = P.recon != nullptr;
+  const bool fast_store = store && full && (P.vec16 & 2);
+  uint32_t acc = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    uint32_t x[8];
-    unpack_row<DT>(rw, k, x);
+    uint32_t n2[8], q[8];
+    inv8<uint32_t>(v + 8 * k, n2);
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
-      const int32_t d = (int32_t)x[l] - out[8 * k + l];
-      const bool valid = full || ((by * 8 + k) < P.H && (bx * 8 + l) < P.W);
-      sse += valid ? (uint32_t)(d * d) : 0u;
+      const int32_t a = (int32_t)n2[l] + ((int32_t)n2[l] >> 31) + kI16Bias;
+      q[l] = min(max((uint32_t)__mulhi(a, kDivMagic) >> 16, 2048u - 255u), 2048u + 255u);
+    }
+    uint32_t x[8];
+    unpack_i16x8(rw.w[k], x);
+    const bool row_in = k < valid_rows;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int32_t d = (int32_t)x[l] + 2048 - (int32_t)q[l];
+      const bool in = full || (row_in && l < valid_cols);
+      acc += in ? (uint32_t)(d * d) : 0u;
+    }
+    if (store && row_in) {
+      // lanes q - 2048 as int16: offset binary (q + 30720, no carry) with the
+      // sign bit flipped
+      uint32_t o[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) o[m] = ((q[2 * m] | (q[2 * m + 1] << 16)) + 0x78007800u) ^ 0x80008000u;
+      uint8_t* row = P.recon + (int64_t)(by * 8 + k) * P.recon_pitch + (int64_t)bx * 16;
+      if (fast_store) {
+        reinterpret_cast<uint2*>(row)[0] = make_uint2(o[0], o[1]);
+        reinterpret_cast<uint2*>(row)[1] = make_uint2(o[2], o[3]);
+      } else {
+#pragma unroll
+        for (int l = 0; l < 8; ++l)
+          if (l < valid_cols)
+            reinterpret_cast<int16_t*>(row)[l] = (int16_t)(o[l >> 1] >> (16 * (l & 1)));
+      }
     }
   }
-  if (P.recon) store_block<DT>(P, by, bx, full && (P.vec16 & 2), out);
-  return sse;
+  return acc;
 }
 
-// Process the two blocks (bx0, bx0 + 1) of block-row `by` owned by a lane.
-// Both blocks are loaded before either is computed.  Returns the lane's SSE.
-// Interior rows need 8-byte alignment of img / recon rows (checked on the
-// host: P.vec16 & 1 for img, & 2 for recon); other blocks use sample loads.
-template <int R, int DT>
-__device__ __forceinline__ uint32_t codec_lane(const PlaneDesc& P, int by, int bx0,
-                                               const CodecParams& cp) {
+// The lane's two int16 blocks (bx0, bx0 + 1) of block-row `by`, one after the
+// other (the second is loaded after the first is done: fewer live registers,
+// more resident warps).
+template <int R>
+__device__ __forceinline__ uint32_t codec_lane_i16(const PlaneDesc& P, int by, int bx0,
+                                                   const CodecParams& cp) {
   const bool has0 = bx0 < P.nbx, has1 = bx0 + 1 < P.nbx;
   if (!has0) return 0u;
-  const bool rows_in = by * 8 + 8 <= P.H;
-  const bool in0 = rows_in && (bx0 + 1) * 8 <= P.W && (P.vec16 & 1);
-  const bool in1 = rows_in && (bx0 + 2) * 8 <= P.W && (P.vec16 & 1);
-  RowWords<DT> ra, rb;
-  load_block<DT>(P, by, bx0, in0, ra);
-  if (has1) load_block<DT>(P, by, bx0 + 1, in1, rb);
-  uint32_t sse = codec_one<R, DT>(P, by, bx0, ra, cp);
-  if (has1) sse += codec_one<R, DT>(P, by, bx0 + 1, rb, cp);
+  const int valid_rows = min(8, P.H - by * 8);
+  uint32_t sse = 0;
+#pragma unroll 1
+  for (int b = 0; b < 2; ++b) {
+    if (b == 1 && !has1) break;
+    const int bx = bx0 + b;
+    const int valid_cols = min(8, P.W - bx * 8);
+    const bool interior = valid_rows == 8 && valid_cols == 8 && (P.vec16 & 1);
+    RowWords<1> rw;
+    load_block<1>(P, by, bx, interior, rw);
+    sse += codec_block_i16<R>(P, by, bx, rw, cp, valid_rows, valid_cols);
+  }
   return sse;
 }
 
@@ -706,14 +745,17 @@ __device__ __forceinline__ uint32_t codec_lane_u8(const PlaneDesc& P, int by, in
 }
 
 // Persistent fused codec: every warp takes a contiguous range of units.
-// Resident CTAs per SM the u8 kernel is compiled for (registers <= 65536 /
-// (256 * TDCT_U8_MINB)); the int16 kernel keeps one.
+// Resident CTAs per SM the kernels are compiled for (registers <= 65536 /
+// (256 * MINB)).
 #ifndef TDCT_U8_MINB
 #define TDCT_U8_MINB 2
 #endif
+#ifndef TDCT_I16_MINB
+#define TDCT_I16_MINB 2
+#endif
 
 template <int R, int DT>
-__global__ void __launch_bounds__(256, DT == 0 ? TDCT_U8_MINB : 1) codec_kernel(const PlaneTable tab, const CodecParams cp,
+__global__ void __launch_bounds__(256, DT == 0 ? TDCT_U8_MINB : TDCT_I16_MINB) codec_kernel(const PlaneTable tab, const CodecParams cp,
                                                     unsigned long long* __restrict__ sse_out) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -747,7 +789,7 @@ __global__ void __launch_bounds__(256, DT == 0 ? TDCT_U8_MINB : 1) codec_kernel(
     }
     if (P.dtype != DT) continue;  // never true for tables the host builds
     if constexpr (DT == 0) acc += codec_lane_u8<R>(P, by, chunk * 64 + 2 * lane, cp);
-    else acc += codec_lane<R, DT>(P, by, chunk * 64 + 2 * lane, cp);
+    else acc += codec_lane_i16<R>(P, by, chunk * 64 + 2 * lane, cp);
   }
   if (p >= 0) {
     acc = warp_sum_u64(acc);
