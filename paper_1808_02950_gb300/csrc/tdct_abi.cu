@@ -233,8 +233,10 @@ PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int
   d.r = r;
   const bool bulk = dtype == TDCT_U8 && ((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch) & 15) == 0 &&
                     W % 16 == 0 && H % 8 == 0 && (!recon || aligned8(recon, recon_pitch));
+  const bool staged = dtype == TDCT_U8 && !bulk && aligned8(img, pitch) && W % 8 == 0 &&
+                      H % 8 == 0 && (!recon || aligned8(recon, recon_pitch));
   d.vec16 = (aligned8(img, pitch) ? 1 : 0) | ((recon && aligned8(recon, recon_pitch)) ? 2 : 0) |
-            (bulk ? 4 : 0);
+            (bulk ? 4 : 0) | (staged ? 8 : 0);
   d.slot = slot;
   return d;
 }
@@ -396,7 +398,8 @@ struct Group {
   int dtype, r;
   int first, count;
   int64_t units;
-  int any_bulk;
+  int any_bulk;  // the planes take the bulk-copy ring
+  int staged;    // the planes take the staged-copy ring
 };
 
 int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& descs,
@@ -415,14 +418,15 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
     if (p.recon && p.recon_pitch < (int64_t)p.W * sample_bytes(p.dtype))
       return fail(TDCT_EINVAL, "plane %d: recon pitch too small", i);
     const PlaneDesc probe = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, p.r, p.recon, p.recon_pitch, i);
-    by_key[{p.dtype, p.r, (probe.vec16 & 4) ? 1 : 0}].push_back(i);
+    by_key[{p.dtype, p.r, (probe.vec16 & 4) ? 1 : (probe.vec16 & 8) ? 2 : 0}].push_back(i);
     npix[i] = (int64_t)p.H * p.W;
   }
   descs.clear();
   groups.clear();
   for (auto& kv : by_key) {
     Group g{std::get<0>(kv.first), std::get<1>(kv.first), (int)descs.size(),
-            (int)kv.second.size(), 0, std::get<2>(kv.first)};
+            (int)kv.second.size(), 0, std::get<2>(kv.first) == 1 ? 1 : 0,
+            std::get<2>(kv.first) == 2 ? 1 : 0};
     for (int i : kv.second) {
       const tdct_plane& p = planes[i];
       PlaneDesc d = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, p.r, p.recon, p.recon_pitch, i);
@@ -449,6 +453,7 @@ cudaError_t enqueue_batch(const Transform& tr, const std::vector<Group>& groups,
     tab.n = g.count;
     tab.total_units = g.units;
     tab.any_bulk = g.any_bulk;
+    tab.staged = g.staged;
     const bool tensor = path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED;
     if (!tr.t1)
       e = dispatch_codec_generic(g.r, g.dtype, tab, tr, sse, s);
@@ -628,6 +633,7 @@ int tdct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype,
   tab.one = make_desc(d_img, pitch, H, W, dtype, r, d_recon, recon_pitch, 0);
   tab.total_units = units_of(tab.one);
   tab.any_bulk = (tab.one.vec16 & 4) ? 1 : 0;
+  tab.staged = (tab.one.vec16 & 8) ? 1 : 0;
   unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error memset");

@@ -31,7 +31,8 @@ struct PlaneDesc {
   int32_t dtype;       // 0 = u8, 1 = i16
   int32_t r;
   int32_t vec16;       // bit 0: img rows 8-byte aligned; bit 1: recon rows;
-                       // bit 2: u8 plane eligible for the bulk-copy ring
+                       // bit 2: u8 plane eligible for the bulk-copy ring;
+                       // bit 3: u8 plane eligible for the staged-copy ring
   int32_t slot;        // output index for SSE / PSNR
   int32_t pad_;
 };
@@ -42,6 +43,8 @@ struct PlaneTable {
   int32_t any_bulk;    // some plane takes the bulk-copy path (vec16 bit 2)
   int64_t total_units;
   PlaneDesc one;
+  int32_t staged;      // the planes take the staged-copy path (vec16 bit 3)
+  int32_t pad_;
 };
 
 __device__ __forceinline__ const PlaneDesc& plane_at(const PlaneTable& t, int i) {
@@ -1026,6 +1029,133 @@ __host__ __device__ constexpr int ring_stages() {
 #endif
 }
 
+// ---- u8 path with a staged-copy ring (rows 8-byte aligned) --------------------
+//
+// For u8 planes whose rows are 8-byte but not 16-byte aligned (or whose width
+// is 8 mod 16), which the bulk-copy engine cannot take.  Same units, slots and
+// work split as the bulk-copy ring, but each lane stages only its own two
+// blocks: 16 `cp.async` copies of 8 bytes per unit (8 rows x 2 blocks), one
+// commit group per unit, `cp.async.wait_group` before the unit is computed.
+// A lane reads only what it copied, so no barrier or mbarrier is involved
+// and every wait completes with the lane's own copies.  Planes need
+// H % 8 == 0 and W % 8 == 0 (every existing block is full; a lane whose
+// second block lies past the right edge copies and codes the first only).
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int R, int STAGES>
+__global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
+    codec_u8_staged_kernel(const PlaneTable tab, const CodecParams cp,
+                           unsigned long long* __restrict__ sse_out) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t* ring = smem + (size_t)wid * STAGES * kUnitBytes;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t U = tab.total_units;
+  const int64_t u_begin = (U * warp) / nwarps;
+  const int n_units = (int)((U * (warp + 1)) / nwarps - u_begin);
+
+  // producer cursor, as in the bulk-copy ring
+  int64_t pp_pitch = 0;
+  const uint8_t* pp_img = nullptr;
+  int pp_end = -1, pp_W = 0, pp_chunks = 1, pp_by = 0, pp_chunk = 0, pp_s = 0;
+  int pf = 0;
+  // stage unit pf (if any) into its slot and close one commit group
+  auto issue_next = [&]() {
+    if (pf < n_units) {
+      const int i = pf++;
+      const int s = pp_s;
+      pp_s = pp_s + 1 == STAGES ? 0 : pp_s + 1;
+      if (i >= pp_end) {
+        const int64_t u = u_begin + i;
+        const int q = find_plane(tab, u);
+        const PlaneDesc& Q = tab.d ? tab.d[q] : tab.one;
+        pp_img = Q.img;
+        pp_pitch = Q.pitch;
+        pp_W = Q.W;
+        pp_chunks = Q.chunks;
+        const int64_t e = ((q + 1 < tab.n) ? tab.d[q + 1].unit_begin : U) - u_begin;
+        pp_end = (int)(e < n_units ? e : n_units);
+        const int64_t local = u - Q.unit_begin;
+        pp_by = (int)(local / pp_chunks);
+        pp_chunk = (int)(local - (int64_t)pp_by * pp_chunks);
+      }
+      const int by = pp_by, chunk = pp_chunk;
+      if (++pp_chunk == pp_chunks) {
+        pp_chunk = 0;
+        ++pp_by;
+      }
+      const int off = chunk * 512 + 16 * lane;  // the lane's first block, bytes into the row
+      if (off < pp_W) {
+        const bool second = off + 8 < pp_W;
+        const uint8_t* src = pp_img + (int64_t)(by * 8) * pp_pitch + off;
+        const uint32_t dst = smem_addr(ring + s * kUnitBytes + lane * 16);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          cp_async8(dst + k * 512, src + (int64_t)k * pp_pitch);
+          if (second) cp_async8(dst + k * 512 + 8, src + (int64_t)k * pp_pitch + 8);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  for (int k = 0; k < STAGES - 1; ++k) issue_next();
+
+  int p = -1;
+  int p_end = -1;
+  PlaneDesc P;
+  int by = 0, chunk = 0, s = 0;  // consumer cursor
+  unsigned long long acc = 0;
+  for (int i = 0; i < n_units; ++i) {
+    if (i >= p_end) {
+      if (p >= 0) {
+        acc = warp_sum_u64(acc);
+        if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+        acc = 0;
+      }
+      const int64_t u = u_begin + i;
+      p = find_plane(tab, u);
+      P = tab.d ? tab.d[p] : tab.one;
+      const int64_t e = ((p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U) - u_begin;
+      p_end = (int)(e < n_units ? e : n_units);
+      const int64_t local = u - P.unit_begin;
+      by = (int)(local / P.chunks);
+      chunk = (int)(local - (int64_t)by * P.chunks);
+    }
+    const int bx0 = chunk * 64 + 2 * lane;
+    const int cur_by = by, cur_s = s;
+    if (++chunk == P.chunks) {
+      chunk = 0;
+      ++by;
+    }
+    s = s + 1 == STAGES ? 0 : s + 1;
+    // unit i + STAGES - 1 goes to the slot of unit i - 1, which this lane has
+    // finished reading; then unit i's group (STAGES - 1 groups older than the
+    // newest) is complete
+    issue_next();
+    cp_async_wait<STAGES - 1>();
+    const uint8_t* slot = ring + cur_s * kUnitBytes + lane * 16;
+    if (bx0 < P.nbx)
+      acc += codec_pair_u8<R, false>(P, cur_by, bx0, RowsInSmem{slot}, RowsInSmem{slot + 8}, cp);
+  }
+  cp_async_wait<0>();
+  if (p >= 0) {
+    acc = warp_sum_u64(acc);
+    if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+  }
+}
+
 inline int device_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -1042,7 +1172,8 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
   constexpr int kRingThreads = TDCT_RING_THREADS;
   constexpr int kStages = ring_stages<R>();
   constexpr size_t kSmem = (size_t)(kRingThreads / 32) * kStages * (kUnitBytes + 8);
-  static int resident = 0, resident_bulk = 0;  // CTAs per SM, computed once
+  constexpr size_t kSmemStaged = (size_t)(kRingThreads / 32) * kStages * kUnitBytes;
+  static int resident = 0, resident_bulk = 0, resident_staged = 0;  // CTAs per SM, computed once
   static int sms = 0;
   if (resident == 0) {
     sms = device_sms();
@@ -1062,13 +1193,25 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
           &resident_bulk, codec_u8_tma_kernel<R, kStages>, kRingThreads, kSmem);
       if (e != cudaSuccess) return e;
       if (resident_bulk < 1) resident_bulk = 1;
+      e = cudaFuncSetAttribute(codec_u8_staged_kernel<R, kStages>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemStaged);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(codec_u8_staged_kernel<R, kStages>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &resident_staged, codec_u8_staged_kernel<R, kStages>, kRingThreads, kSmemStaged);
+      if (e != cudaSuccess) return e;
+      if (resident_staged < 1) resident_staged = 1;
     }
   }
   const bool bulk = DT == 0 && tab.any_bulk;
-  int per_sm = bulk ? resident_bulk : resident;
+  const bool staged = DT == 0 && !bulk && tab.staged;
+  int per_sm = bulk ? resident_bulk : staged ? resident_staged : resident;
   if (cp.ctas_per_sm > 0 && cp.ctas_per_sm < per_sm) per_sm = cp.ctas_per_sm;
   int64_t grid = (int64_t)per_sm * sms;
-  const int threads = bulk ? kRingThreads : kThreads;
+  const int threads = (bulk || staged) ? kRingThreads : kThreads;
   const int64_t by_work = (tab.total_units + threads / 32 - 1) / (threads / 32);
   if (by_work < grid) grid = by_work;
   if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
@@ -1076,6 +1219,11 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
   if constexpr (DT == 0) {
     if (bulk) {
       codec_u8_tma_kernel<R, kStages><<<(unsigned)grid, kRingThreads, kSmem, s>>>(tab, cp, sse);
+      return cudaGetLastError();
+    }
+    if (staged) {
+      codec_u8_staged_kernel<R, kStages><<<(unsigned)grid, kRingThreads, kSmemStaged, s>>>(tab, cp,
+                                                                                         sse);
       return cudaGetLastError();
     }
   }

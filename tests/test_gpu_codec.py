@@ -253,6 +253,42 @@ def test_bulk_copy_ring_many_units_per_warp():
         assert np.array_equal(recons[i].cpu().numpy(), want_rec)
 
 
+@pytest.mark.parametrize("H,W", [(8, 8), (16, 24), (64, 1032), (48, 2056), (8, 4104)])
+def test_staged_copy_ring_planes(H, W):
+    """u8 planes with 8-byte aligned rows, W % 16 == 8 and H % 8 == 0 take the
+    staged-copy ring (the last lane of a row codes one block only)."""
+    rng = np.random.default_rng(H * 11 + W)
+    host = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    img = torch.from_numpy(host).to(DEV)
+    for r in (1, 10, 16, 40, 64):
+        sse, rec, _ = run_codec(img, r)
+        want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+        assert np.array_equal(rec, want_rec) and sse == want_sse
+        sse2, _, _ = run_codec(img, r, want_recon=False)
+        assert sse2 == want_sse
+
+
+def test_staged_bulk_and_plain_planes_in_one_batch():
+    """Bulk-copy, staged-copy and plain planes with mixed r in one batch, enough
+    units that every warp walks its ring many times."""
+    rng = np.random.default_rng(77)
+    sizes = [(1024, 1032)] * 10 + [(1024, 1024)] * 10 + [(1023, 1033)] * 3 + [(520, 8), (8, 520)]
+    hosts, views, rs = [], [], []
+    for i, (H, W) in enumerate(sizes):
+        h = rng.integers(0, 256, (H, W)).astype(np.uint8)
+        hosts.append(h)
+        views.append(torch.from_numpy(h).to(DEV))
+        rs.append((4, 8, 16, 32)[i % 4])
+    recons = [torch.full_like(v, 5) for v in views]
+    sse = torch.zeros(len(views), dtype=torch.int64, device=DEV)
+    P.tdct_codec_error_batched(P.make_planes(views, rs, recons), sse)
+    torch.cuda.synchronize()
+    for i in (0, 9, 10, 19, 20, 22, 23, 24):
+        want_sse, want_rec, _ = oc.codec_plane(hosts[i], M.T1, rs[i])
+        assert int(sse[i]) == want_sse, i
+        assert np.array_equal(recons[i].cpu().numpy(), want_rec), i
+
+
 def test_bounded_wait_timeout_is_reported_and_context_survives():
     """A withheld bulk copy makes one warp's bounded wait give up: the library
     reports TDCT_ETIMEOUT through the status word, nothing hangs, and the
