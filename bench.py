@@ -15,6 +15,13 @@ synchronisation, CUDA events on the launching stream; the max over ranks.
 With N > 1 (torchrun) every rank runs its own replica of the workload
 (weak scaling, no collective on the data path).  Rank 0 prints one JSON
 line.  ``--impl reference`` times the CPU oracle on host cores instead.
+
+Besides the step, the default run reports on the same images: ``e2e`` (the
+host-buffer call with its copies), ``ssim`` (mean SSIM of original vs
+reconstruction), ``jam`` (16x16 and 32x32 blocks with the JAM matrices),
+``dct`` (the exact-DCT comparison codec, FP32 and BF16) and ``search`` (the
+greedy angle search, N = 16 and 12); ``--no-e2e``, ``--no-ssim``,
+``--no-jam``, ``--no-dct`` and ``--no-search`` skip them.
 """
 from __future__ import annotations
 
@@ -54,6 +61,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-jam", action="store_true",
                     help="skip the 16x16 / 32x32 JAM codec timing")
+    ap.add_argument("--no-dct", action="store_true",
+                    help="skip the exact-DCT comparison codec timing (FP32 and BF16)")
     ap.add_argument("--no-search", action="store_true",
                     help="skip the angle-search timing (N = 16 and N = 12, P = {-1, 0, 1})")
     ap.add_argument("--no-ssim", action="store_true",
@@ -424,6 +433,33 @@ def time_ours(args, dist, out):
             jam[f"B{B}"] = {"ms": ms, "r": wl.desc["r"], "pixels_per_s": big.numel() / (ms / 1e3),
                             "hbm_gbs": gbs, "frac_of_measured_hbm": gbs / measured_peaks()[0]}
         out["jam"] = jam
+    # The exact-DCT comparison codec (orthonormal DCT-II in FP32, or with
+    # BF16-rounded inputs, constants and kept coefficients) on the same images
+    # as one tall plane, reconstruction written.
+    if not args.no_dct and args.workload == "batch_1024x1024" and args.transform == "T1":
+        big = wl.storage[0].view(-1, wl.storage[0].shape[-1])
+        rec_big = torch.empty_like(big)
+        dsse = torch.zeros(1, dtype=torch.int64, device=dev)
+        dct = {}
+        for name, prec in (("fp32", P.TDCT_FP32), ("bf16", P.TDCT_BF16)):
+            for _ in range(2):
+                P.tdct_dct_codec_error(big, wl.desc["r"], dsse, precision=prec, recon=rec_big,
+                                       stream=stream)
+            torch.cuda.synchronize()
+            d0 = torch.cuda.Event(enable_timing=True)
+            d1 = torch.cuda.Event(enable_timing=True)
+            d0.record(stream)
+            for _ in range(5):
+                P.tdct_dct_codec_error(big, wl.desc["r"], dsse, precision=prec, recon=rec_big,
+                                       stream=stream)
+            d1.record(stream)
+            torch.cuda.synchronize()
+            ms = d0.elapsed_time(d1) / 5
+            blocks = big.numel() // 64
+            gbs = 2 * big.numel() / (ms / 1e3) / 1e9
+            dct[name] = {"ms": ms, "r": wl.desc["r"], "blocks_per_s": blocks / (ms / 1e3),
+                         "hbm_gbs": gbs, "frac_of_measured_hbm": gbs / measured_peaks()[0]}
+        out["dct"] = dct
     plan.close()
     return wl
 
