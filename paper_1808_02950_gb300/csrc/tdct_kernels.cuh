@@ -32,7 +32,7 @@ struct PlaneDesc {
   int32_t r;
   int32_t vec16;       // bit 0: img rows 8-byte aligned; bit 1: recon rows;
                        // bit 2: u8 plane eligible for the bulk-copy ring;
-                       // bit 3: u8 plane eligible for the staged-copy ring
+                       // bit 3: plane eligible for a staged-copy ring (u8 or int16)
   int32_t slot;        // output index for SSE / PSNR
   int32_t pad_;
 };
@@ -43,7 +43,7 @@ struct PlaneTable {
   int32_t any_bulk;    // some plane takes the bulk-copy path (vec16 bit 2)
   int64_t total_units;
   PlaneDesc one;
-  int32_t staged;      // the planes take the staged-copy path (vec16 bit 3)
+  int32_t staged;      // the planes take a staged-copy ring (vec16 bit 3)
   int32_t pad_;
 };
 
@@ -278,16 +278,30 @@ __device__ __forceinline__ void load_block(const PlaneDesc& P, int by, int bx, b
 // offset quotient is clamped to 2048 +- 255.
 constexpr int32_t kI16Bias = (int32_t)(kL2 + 2048u * 2u * kL2);
 
-template <int R>
-__device__ __forceinline__ uint32_t codec_block_i16(const PlaneDesc& P, int by, int bx,
-                                                    const RowWords<1>& rw, const CodecParams& cp,
-                                                    int valid_rows, int valid_cols) {
+// Where the int16 codec reads a block's row k (8 samples in a uint4): the row
+// words in registers, or a staged-copy slot in shared memory (row stride
+// 1024 B), re-read for the SSE instead of being held across the inverse.
+struct I16RowsInRegs {
+  const uint4* w;
+  __device__ __forceinline__ uint4 row(int k) const { return w[k]; }
+};
+struct I16RowsInSmem {
+  const uint8_t* p;
+  __device__ __forceinline__ uint4 row(int k) const {
+    return *reinterpret_cast<const uint4*>(p + k * 1024);
+  }
+};
+
+template <int R, typename RS>
+__device__ __forceinline__ uint32_t codec_block_i16(const PlaneDesc& P, int by, int bx, RS rw,
+                                                    const CodecParams& cp, int valid_rows,
+                                                    int valid_cols) {
   const bool full = valid_rows == 8 && valid_cols == 8;
   uint32_t w[64];
   {
     uint32_t x[64], z[64];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) unpack_i16x8(rw.w[k], x + 8 * k);
+    for (int k = 0; k < 8; ++k) unpack_i16x8(rw.row(k), x + 8 * k);
     fwd2d<uint32_t>(x, z);
 #pragma unroll
     for (int p = 0; p < 64; ++p)
@@ -317,7 +331,7 @@ __device__ __forceinline__ uint32_t codec_block_i16(const PlaneDesc& P, int by, 
       q[l] = min(max((uint32_t)__mulhi(a, kDivMagic) >> 16, 2048u - 255u), 2048u + 255u);
     }
     uint32_t x[8];
-    unpack_i16x8(rw.w[k], x);
+    unpack_i16x8(rw.row(k), x);
     const bool row_in = k < valid_rows;
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
@@ -364,7 +378,7 @@ __device__ __forceinline__ uint32_t codec_lane_i16(const PlaneDesc& P, int by, i
     const bool interior = valid_rows == 8 && valid_cols == 8 && (P.vec16 & 1);
     RowWords<1> rw;
     load_block<1>(P, by, bx, interior, rw);
-    sse += codec_block_i16<R>(P, by, bx, rw, cp, valid_rows, valid_cols);
+    sse += codec_block_i16<R>(P, by, bx, I16RowsInRegs{rw.w}, cp, valid_rows, valid_cols);
   }
   return sse;
 }
@@ -1156,6 +1170,132 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
   }
 }
 
+// int16 residual planes with 8-byte aligned rows and W % 8 == 0, any H: the
+// staged-copy ring with 8 KB units (8 rows x 64 blocks x 16 B).  A lane
+// stages its two blocks (32 copies of 8 bytes; rows past the bottom edge are
+// zero-filled in shared memory, the residual pad) and codes them one after
+// the other from the slot.  Two slots per warp (3 CTAs x 4 warps x 16 KB).
+constexpr int kUnitBytesI16 = 8 * 1024;
+constexpr int kStagesI16 = 2;
+
+template <int R>
+__global__ void __launch_bounds__(TDCT_RING_THREADS, 3)
+    codec_i16_staged_kernel(const PlaneTable tab, const CodecParams cp,
+                            unsigned long long* __restrict__ sse_out) {
+  constexpr int STAGES = kStagesI16;
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t* ring = smem + (size_t)wid * STAGES * kUnitBytesI16;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t U = tab.total_units;
+  const int64_t u_begin = (U * warp) / nwarps;
+  const int n_units = (int)((U * (warp + 1)) / nwarps - u_begin);
+
+  int64_t pp_pitch = 0;
+  const uint8_t* pp_img = nullptr;
+  int pp_end = -1, pp_W = 0, pp_H = 0, pp_chunks = 1, pp_by = 0, pp_chunk = 0, pp_s = 0;
+  int pf = 0;
+  auto issue_next = [&]() {
+    if (pf < n_units) {
+      const int i = pf++;
+      const int s = pp_s;
+      pp_s = pp_s + 1 == STAGES ? 0 : pp_s + 1;
+      if (i >= pp_end) {
+        const int64_t u = u_begin + i;
+        const int q = find_plane(tab, u);
+        const PlaneDesc& Q = tab.d ? tab.d[q] : tab.one;
+        pp_img = Q.img;
+        pp_pitch = Q.pitch;
+        pp_W = Q.W;
+        pp_H = Q.H;
+        pp_chunks = Q.chunks;
+        const int64_t e = ((q + 1 < tab.n) ? tab.d[q + 1].unit_begin : U) - u_begin;
+        pp_end = (int)(e < n_units ? e : n_units);
+        const int64_t local = u - Q.unit_begin;
+        pp_by = (int)(local / pp_chunks);
+        pp_chunk = (int)(local - (int64_t)pp_by * pp_chunks);
+      }
+      const int by = pp_by, chunk = pp_chunk;
+      if (++pp_chunk == pp_chunks) {
+        pp_chunk = 0;
+        ++pp_by;
+      }
+      const int bx0 = chunk * 64 + 2 * lane;  // the lane's first block
+      if (bx0 * 8 < pp_W) {
+        const bool second = (bx0 + 1) * 8 < pp_W;
+        const uint8_t* src = pp_img + (int64_t)(by * 8) * pp_pitch + (int64_t)bx0 * 16;
+        uint8_t* slot = ring + s * kUnitBytesI16 + lane * 32;
+        const uint32_t dst = smem_addr(slot);
+        const int rows = min(8, pp_H - by * 8);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (k < rows) {
+            const uint8_t* sk = src + (int64_t)k * pp_pitch;
+            cp_async8(dst + k * 1024, sk);
+            cp_async8(dst + k * 1024 + 8, sk + 8);
+            if (second) {
+              cp_async8(dst + k * 1024 + 16, sk + 16);
+              cp_async8(dst + k * 1024 + 24, sk + 24);
+            }
+          } else {
+            *reinterpret_cast<uint4*>(slot + k * 1024) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(slot + k * 1024 + 16) = make_uint4(0u, 0u, 0u, 0u);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  for (int k = 0; k < STAGES - 1; ++k) issue_next();
+
+  int p = -1;
+  int p_end = -1;
+  PlaneDesc P;
+  int by = 0, chunk = 0, s = 0;
+  unsigned long long acc = 0;
+  for (int i = 0; i < n_units; ++i) {
+    if (i >= p_end) {
+      if (p >= 0) {
+        acc = warp_sum_u64(acc);
+        if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+        acc = 0;
+      }
+      const int64_t u = u_begin + i;
+      p = find_plane(tab, u);
+      P = tab.d ? tab.d[p] : tab.one;
+      const int64_t e = ((p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U) - u_begin;
+      p_end = (int)(e < n_units ? e : n_units);
+      const int64_t local = u - P.unit_begin;
+      by = (int)(local / P.chunks);
+      chunk = (int)(local - (int64_t)by * P.chunks);
+    }
+    const int bx0 = chunk * 64 + 2 * lane;
+    const int cur_by = by, cur_s = s;
+    if (++chunk == P.chunks) {
+      chunk = 0;
+      ++by;
+    }
+    s = s + 1 == STAGES ? 0 : s + 1;
+    issue_next();  // into the slot of unit i - 1, which this lane has finished reading
+    cp_async_wait<STAGES - 1>();
+    const uint8_t* slot = ring + cur_s * kUnitBytesI16 + lane * 32;
+    const int valid_rows = min(8, P.H - cur_by * 8);
+#pragma unroll 1
+    for (int b = 0; b < 2; ++b) {
+      if (bx0 + b < P.nbx)
+        acc += codec_block_i16<R>(P, cur_by, bx0 + b, I16RowsInSmem{slot + 16 * b}, cp, valid_rows, 8);
+    }
+  }
+  cp_async_wait<0>();
+  if (p >= 0) {
+    acc = warp_sum_u64(acc);
+    if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+  }
+}
+
 inline int device_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -1204,6 +1344,35 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
           &resident_staged, codec_u8_staged_kernel<R, kStages>, kRingThreads, kSmemStaged);
       if (e != cudaSuccess) return e;
       if (resident_staged < 1) resident_staged = 1;
+    }
+  }
+  if constexpr (DT == 1) {
+    if (tab.staged) {
+      constexpr size_t kSmemI16 = (size_t)(kRingThreads / 32) * kStagesI16 * kUnitBytesI16;
+      static int resident_i16 = 0;
+      if (resident_i16 == 0) {
+        cudaError_t e = cudaFuncSetAttribute(codec_i16_staged_kernel<R>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemI16);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(codec_i16_staged_kernel<R>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident_i16, codec_i16_staged_kernel<R>,
+                                                          kRingThreads, kSmemI16);
+        if (e != cudaSuccess) return e;
+        if (resident_i16 < 1) resident_i16 = 1;
+      }
+      int per_sm = resident_i16;
+      if (cp.ctas_per_sm > 0 && cp.ctas_per_sm < per_sm) per_sm = cp.ctas_per_sm;
+      int64_t grid = (int64_t)per_sm * sms;
+      const int64_t by_work = (tab.total_units + kRingThreads / 32 - 1) / (kRingThreads / 32);
+      if (by_work < grid) grid = by_work;
+      if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+      if (grid < 1) grid = 1;
+      codec_i16_staged_kernel<R><<<(unsigned)grid, kRingThreads, kSmemI16, s>>>(tab, cp, sse);
+      return cudaGetLastError();
     }
   }
   const bool bulk = DT == 0 && tab.any_bulk;

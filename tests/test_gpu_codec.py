@@ -268,6 +268,22 @@ def test_staged_copy_ring_planes(H, W):
         assert sse2 == want_sse
 
 
+@pytest.mark.parametrize("H,W", [(8, 8), (13, 16), (540, 960), (64, 1032), (1080, 1920)])
+def test_int16_staged_copy_ring_planes(H, W):
+    """int16 residual planes with 8-byte aligned rows and W % 8 == 0 take the
+    int16 staged-copy ring; heights that are not multiples of 8 (the 540-row
+    chroma planes) are zero-padded in shared memory."""
+    rng = np.random.default_rng(H * 13 + W)
+    host = rng.integers(-255, 256, (H, W)).astype(np.int16)
+    img = torch.from_numpy(host).to(DEV)
+    for r in ((8, 16) if H * W > 100000 else (1, 8, 16, 40, 64)):
+        sse, rec, _ = run_codec(img, r)
+        want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+        assert np.array_equal(rec, want_rec) and sse == want_sse
+        sse2, _, _ = run_codec(img, r, want_recon=False)
+        assert sse2 == want_sse
+
+
 def test_staged_bulk_and_plain_planes_in_one_batch():
     """Bulk-copy, staged-copy and plain planes with mixed r in one batch, enough
     units that every warp walks its ring many times."""
