@@ -233,10 +233,11 @@ PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int
   d.r = r;
   const bool bulk = dtype == TDCT_U8 && ((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch) & 15) == 0 &&
                     W % 16 == 0 && H % 8 == 0 && (!recon || aligned8(recon, recon_pitch));
-  // staged-copy rings: u8 planes that miss the bulk-copy conditions (H % 8 == 0),
-  // int16 planes of any height (rows past the bottom edge are zero-filled)
+  // staged-copy rings: planes that miss the bulk-copy conditions, with 8-byte
+  // aligned rows and W % 8 == 0, any height (rows past the bottom edge are
+  // zero-filled in shared memory)
   const bool staged = !bulk && aligned8(img, pitch) && W % 8 == 0 &&
-                      (dtype == TDCT_I16 || H % 8 == 0) && (!recon || aligned8(recon, recon_pitch));
+                      (!recon || aligned8(recon, recon_pitch));
   d.vec16 = (aligned8(img, pitch) ? 1 : 0) | ((recon && aligned8(recon, recon_pitch)) ? 2 : 0) |
             (bulk ? 4 : 0) | (staged ? 8 : 0);
   d.slot = slot;

@@ -1052,8 +1052,9 @@ __host__ __device__ constexpr int ring_stages() {
 // commit group per unit, `cp.async.wait_group` before the unit is computed.
 // A lane reads only what it copied, so no barrier or mbarrier is involved
 // and every wait completes with the lane's own copies.  Planes need
-// H % 8 == 0 and W % 8 == 0 (every existing block is full; a lane whose
-// second block lies past the right edge copies and codes the first only).
+// W % 8 == 0 (a lane whose second block lies past the right edge copies and
+// codes the first only); rows past the bottom edge are zero-filled in shared
+// memory, the pad of partial blocks.
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -1082,7 +1083,7 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
   // producer cursor, as in the bulk-copy ring
   int64_t pp_pitch = 0;
   const uint8_t* pp_img = nullptr;
-  int pp_end = -1, pp_W = 0, pp_chunks = 1, pp_by = 0, pp_chunk = 0, pp_s = 0;
+  int pp_end = -1, pp_W = 0, pp_H = 0, pp_chunks = 1, pp_by = 0, pp_chunk = 0, pp_s = 0;
   int pf = 0;
   // stage unit pf (if any) into its slot and close one commit group
   auto issue_next = [&]() {
@@ -1097,6 +1098,7 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
         pp_img = Q.img;
         pp_pitch = Q.pitch;
         pp_W = Q.W;
+        pp_H = Q.H;
         pp_chunks = Q.chunks;
         const int64_t e = ((q + 1 < tab.n) ? tab.d[q + 1].unit_begin : U) - u_begin;
         pp_end = (int)(e < n_units ? e : n_units);
@@ -1113,11 +1115,17 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
       if (off < pp_W) {
         const bool second = off + 8 < pp_W;
         const uint8_t* src = pp_img + (int64_t)(by * 8) * pp_pitch + off;
-        const uint32_t dst = smem_addr(ring + s * kUnitBytes + lane * 16);
+        uint8_t* slot = ring + s * kUnitBytes + lane * 16;
+        const uint32_t dst = smem_addr(slot);
+        const int rows = min(8, pp_H - by * 8);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          cp_async8(dst + k * 512, src + (int64_t)k * pp_pitch);
-          if (second) cp_async8(dst + k * 512 + 8, src + (int64_t)k * pp_pitch + 8);
+          if (k < rows) {
+            cp_async8(dst + k * 512, src + (int64_t)k * pp_pitch);
+            if (second) cp_async8(dst + k * 512 + 8, src + (int64_t)k * pp_pitch + 8);
+          } else {
+            *reinterpret_cast<uint4*>(slot + k * 512) = make_uint4(0u, 0u, 0u, 0u);
+          }
         }
       }
     }

@@ -253,10 +253,13 @@ def test_bulk_copy_ring_many_units_per_warp():
         assert np.array_equal(recons[i].cpu().numpy(), want_rec)
 
 
-@pytest.mark.parametrize("H,W", [(8, 8), (16, 24), (64, 1032), (48, 2056), (8, 4104)])
+@pytest.mark.parametrize("H,W", [(8, 8), (16, 24), (64, 1032), (48, 2056), (8, 4104), (13, 16),
+                                 (540, 968), (7, 1032), (1, 8)])
 def test_staged_copy_ring_planes(H, W):
-    """u8 planes with 8-byte aligned rows, W % 16 == 8 and H % 8 == 0 take the
-    staged-copy ring (the last lane of a row codes one block only)."""
+    """u8 planes with 8-byte aligned rows and W % 8 == 0 that miss the bulk-copy
+    conditions (W % 16 == 8 or H % 8 != 0) take the staged-copy ring (the last
+    lane of a row may code one block only; rows past the bottom edge are
+    zero-filled)."""
     rng = np.random.default_rng(H * 11 + W)
     host = rng.integers(0, 256, (H, W)).astype(np.uint8)
     img = torch.from_numpy(host).to(DEV)
