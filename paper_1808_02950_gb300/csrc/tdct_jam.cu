@@ -209,26 +209,18 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   // rows are fetched one iteration ahead: the loads of the next blocks are
   // in flight while the current ones are transformed (measured 8 % faster at
   // B = 16, 5 % at B = 32)
-  constexpr bool kPrefetch = true;
   RowRaw<B, DT> raw_next;
   Geo g_next{};
-  if (kPrefetch && warp * BPW < nb) {
+  if (warp * BPW < nb) {
     g_next = geo_of(warp * BPW);
     fetch_row(g_next, raw_next);
   }
   for (int64_t base = warp * BPW; base < nb; base += nwarps * BPW) {
-    Geo g;
-    RowRaw<B, DT> raw;  // the raw row stays for the error
-    if constexpr (kPrefetch) {
-      g = g_next;
-      raw = raw_next;
-      if (base + nwarps * BPW < nb) {
-        g_next = geo_of(base + nwarps * BPW);
-        fetch_row(g_next, raw_next);
-      }
-    } else {
-      g = geo_of(base);
-      fetch_row(g, raw);
+    const Geo g = g_next;
+    const RowRaw<B, DT> raw = raw_next;  // the raw row stays for the error
+    if (base + nwarps * BPW < nb) {
+      g_next = geo_of(base + nwarps * BPW);
+      fetch_row(g_next, raw_next);
     }
     const bool valid = g.valid, full = g.full;
     const int by = g.by, bx = g.bx;
