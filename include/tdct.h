@@ -198,8 +198,8 @@ int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, cons
  *   planes    host array of nplanes descriptors whose img / recon are HOST
  *             pointers (recon may be NULL: no reconstruction is copied back).
  *             Page-locked memory lets the copies run at the link's rate and
- *             asynchronously; pageable memory works through the driver's
- *             staging.
+ *             asynchronously; pageable memory works through the CUDA
+ *             driver's staging.
  *   h_sse     host output, uint64 [nplanes]
  *   h_psnr    host output or NULL, double [nplanes]
  * Asynchronous on `stream`: outputs and reconstructions are complete when

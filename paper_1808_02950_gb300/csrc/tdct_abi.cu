@@ -915,7 +915,7 @@ cudaError_t copy_planes(const tdct_plane* planes, int first, int count, uint8_t*
     };
     cudaError_t e = linear_copy(i, bytes);
     if (e == cudaErrorInvalidValue && m > k + 1) {
-      // Adjacent planes from different host allocations: the driver rejects
+      // Adjacent planes from different host allocations: the CUDA driver rejects
       // a range that crosses page-locked allocations (argument check,
       // nothing enqueued).  Clear that error and copy the run plane by plane.
       (void)cudaGetLastError();
