@@ -11,7 +11,7 @@
 // stay below 2^14, which keeps the FP32 differences E[x^2] - mx^2 accurate.
 //
 // Work: a unit is a strip of 64 output columns (two adjacent ones per lane)
-// by 128 output rows of one plane; units are dealt to persistent warps as
+// by 512 output rows of one plane; units are dealt to persistent warps as
 // contiguous ranges.  For each input row the warp stages its 74 centred
 // (x, y) pairs in shared memory (each sample loaded one row ahead of its
 // use); each lane reads its 12 input columns once, forms their squares and

@@ -23,7 +23,8 @@ def gpu_mssim(pairs):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("H,W", [(11, 11), (20, 33), (64, 64), (37, 50), (130, 300), (139, 43)])
+@pytest.mark.parametrize("H,W", [(11, 11), (20, 33), (64, 64), (37, 50), (130, 300), (139, 43),
+                                 (533, 40), (1100, 90)])
 def test_ssim_random_pairs(H, W):
     rng = np.random.default_rng(H * 7 + W)
     x = rng.integers(0, 256, (H, W)).astype(np.uint8)
