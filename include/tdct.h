@@ -316,6 +316,28 @@ int tdct_plan_config(const tdct_plan* plan, int* path, int* ctas_per_sm, float* 
 int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stream_t stream);
 /* Kernel launches one tdct_plan_launch performs (for launch accounting). */
 int tdct_plan_kernel_count(const tdct_plan* plan);
+
+/*
+ * How a plan's planes are grouped into codec launches (no counterpart in the
+ * paper; introspection for callers and tests).  One entry per launch: the
+ * sample type, r, the number of planes and how the samples reach the kernel:
+ *   TDCT_LOAD_BULK    per-warp shared-memory ring filled by bulk copies
+ *                     (u8, 16-byte aligned rows, W % 16 == 0, H % 8 == 0);
+ *   TDCT_LOAD_STAGED  per-warp shared-memory ring filled by 8-byte cp.async
+ *                     copies (8-byte aligned rows, W % 8 == 0, any H);
+ *   TDCT_LOAD_PLAIN   plain global loads (all other planes; every plane when
+ *                     T != T1, whose generic kernels load directly).
+ * Writes min(max, groups) entries to `out` and the number of groups to
+ * *count.  Errors: TDCT_EINVAL (NULL plan or count, max < 0).
+ */
+enum tdct_load { TDCT_LOAD_PLAIN = 0, TDCT_LOAD_BULK = 1, TDCT_LOAD_STAGED = 2 };
+typedef struct {
+  int32_t dtype;   /* tdct_dtype */
+  int32_t r;
+  int32_t load;    /* tdct_load */
+  int32_t planes;
+} tdct_plan_group;
+int tdct_plan_groups(const tdct_plan* plan, tdct_plan_group* out, int max, int* count);
 void tdct_plan_destroy(tdct_plan* plan);
 
 /*

@@ -17,6 +17,7 @@ TDCT_ETIMEOUT, TDCT_EDEVICE, TDCT_ENOMEM, TDCT_EUNSUPPORTED = 4, 5, 6, 7
 TDCT_U8, TDCT_I16 = 0, 1
 TDCT_FP32, TDCT_BF16 = 0, 1
 TDCT_PATH_AUTO, TDCT_PATH_BUTTERFLY, TDCT_PATH_TENSOR, TDCT_PATH_TENSOR_PIPELINED = 0, 1, 2, 3
+TDCT_LOAD_PLAIN, TDCT_LOAD_BULK, TDCT_LOAD_STAGED = 0, 1, 2
 
 # T1 of §4.1 and n = diag(T1 T1^T), the arguments the paper states (S = diag(1/sqrt(n))).
 T1 = (
@@ -36,6 +37,7 @@ EXPORTS = (
     "tdct_codec_error_batched_noalloc", "tdct_codec_error_batched_host", "tdct_ssim_batched",
     "tdct_search", "tdct_codec_error_jam",
     "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_config",
+    "tdct_plan_groups",
     "tdct_plan_destroy",
     "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
     "tdct_debug_search_hit_cap",
@@ -55,6 +57,11 @@ class TdctPlane(ctypes.Structure):
         ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("r", ctypes.c_int32),
         ("dtype", ctypes.c_int32), ("recon", ctypes.c_void_p), ("recon_pitch", ctypes.c_int64),
     ]
+
+
+class TdctPlanGroup(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("r", ctypes.c_int32), ("load", ctypes.c_int32),
+                ("planes", ctypes.c_int32)]
 
 
 _lib = None
@@ -90,6 +97,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_plan_kernel_count.argtypes = [vp]
     L.tdct_plan_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_float)]
+    L.tdct_plan_groups.argtypes = [vp, ctypes.POINTER(TdctPlanGroup), i32, ctypes.POINTER(ctypes.c_int)]
     L.tdct_plan_destroy.argtypes = [vp]
     L.tdct_plan_destroy.restype = None
     L.tdct_dct_codec_error.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp, vp, i64, vp, vp, vp]
@@ -307,6 +315,16 @@ class TdctPlan:
                  TDCT_PATH_TENSOR_PIPELINED: "tensor_pipelined"}
         return {"path": names.get(path.value, path.value), "ctas_per_sm": cps.value,
                 "tuned_ms": ms.value}
+
+    def groups(self) -> list:
+        """One dict per codec launch: dtype, r, load path, number of planes."""
+        n = ctypes.c_int()
+        _check(load().tdct_plan_groups(self._h, None, 0, ctypes.byref(n)))
+        arr = (TdctPlanGroup * max(n.value, 1))()
+        _check(load().tdct_plan_groups(self._h, arr, n.value, ctypes.byref(n)))
+        loads = {TDCT_LOAD_PLAIN: "plain", TDCT_LOAD_BULK: "bulk", TDCT_LOAD_STAGED: "staged"}
+        return [{"dtype": "u8" if g.dtype == TDCT_U8 else "i16", "r": g.r,
+                 "load": loads.get(g.load, g.load), "planes": g.planes} for g in arr[:n.value]]
 
     def close(self) -> None:
         if self._h:

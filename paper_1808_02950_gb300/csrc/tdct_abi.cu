@@ -752,6 +752,23 @@ int tdct_plan_config(const tdct_plan* plan, int* path, int* ctas_per_sm, float* 
   return TDCT_OK;
 }
 
+int tdct_plan_groups(const tdct_plan* plan, tdct_plan_group* out, int max, int* count) {
+  if (!plan || !count || max < 0) return fail(TDCT_EINVAL, "plan or count NULL, or max < 0");
+  const int n = (int)plan->groups.size();
+  *count = n;
+  for (int i = 0; i < n && i < max && out; ++i) {
+    const Group& g = plan->groups[i];
+    out[i].dtype = g.dtype;
+    out[i].r = g.r;
+    out[i].load = !plan->tr.t1 ? TDCT_LOAD_PLAIN
+                  : g.any_bulk ? TDCT_LOAD_BULK
+                  : g.staged   ? TDCT_LOAD_STAGED
+                               : TDCT_LOAD_PLAIN;
+    out[i].planes = g.count;
+  }
+  return TDCT_OK;
+}
+
 int tdct_plan_kernel_count(const tdct_plan* plan) {
   return plan ? (int)plan->groups.size() + 1 : 0;
 }

@@ -308,6 +308,28 @@ def test_staged_bulk_and_plain_planes_in_one_batch():
         assert np.array_equal(recons[i].cpu().numpy(), want_rec), i
 
 
+def test_plan_routes_planes_to_the_intended_load_paths():
+    """Bulk-copy ring for 16-byte aligned u8 rows with W % 16 == 0 and
+    H % 8 == 0; staged-copy ring for other 8-byte aligned rows with W % 8 == 0
+    (u8 and int16, any height); plain loads otherwise."""
+    u8 = lambda H, W: torch.zeros(H, W, dtype=torch.uint8, device=DEV)
+    i16 = lambda H, W: torch.zeros(H, W, dtype=torch.int16, device=DEV)
+    odd_pitch = torch.zeros(64 * 132, dtype=torch.int16, device=DEV)[2:2 + 64 * 130].view(64, 130)
+    cases = [(u8(64, 1024), "u8", 3, "bulk"), (u8(64, 1032), "u8", 4, "staged"),
+             (u8(60, 1024), "u8", 5, "staged"), (u8(64, 1030), "u8", 6, "plain"),
+             (i16(540, 960), "i16", 7, "staged"), (odd_pitch[:, :128], "i16", 9, "plain")]
+    planes = P.make_planes([c[0] for c in cases], [c[2] for c in cases])
+    plan = P.tdct_plan_create(planes, path=P.TDCT_PATH_BUTTERFLY)
+    try:
+        got = {(g["dtype"], g["r"]): (g["load"], g["planes"]) for g in plan.groups()}
+        assert len(got) == len(cases)
+        for _, dt, r, load in cases:
+            assert got[(dt, r)] == (load, 1), (dt, r, got[(dt, r)])
+        assert plan.kernel_count() == len(cases) + 1  # + the PSNR kernel
+    finally:
+        plan.close()
+
+
 def test_bounded_wait_timeout_is_reported_and_context_survives():
     """A withheld bulk copy makes one warp's bounded wait give up: the library
     reports TDCT_ETIMEOUT through the status word, nothing hangs, and the
