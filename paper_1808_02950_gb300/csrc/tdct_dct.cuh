@@ -68,14 +68,41 @@ __device__ __forceinline__ void dct8_inv(const float y[8], float x[8], const flo
   }
 }
 
-template <int DT>
+// floor(t) for |t| < 2^22 without the conversion pipe: t + 1.5 * 2^23 rounded
+// toward -inf has unit spacing, so its bit pattern is 0x4B400000 + floor(t).
+__device__ __forceinline__ int32_t floor_small(float t) {
+  return __float_as_int(__fadd_rd(t, 12582912.0f)) - 0x4B400000;
+}
+
+// An integer sample |x| < 2^22 as a float, exactly, without the conversion
+// pipe: the bit pattern 0x4B000000 + (x + 2^15) is 2^23 + x + 2^15.
+__device__ __forceinline__ float small_int_to_float(int32_t x) {
+  return __int_as_float(0x4B000000 + (x + 32768)) - 8421376.0f;
+}
+
+// floor(t) by the conversion instruction (FP32 path) or by the bit pattern
+// (BF16 path); both are exact for the values here.  Measured: the FP32 codec
+// is 2 % faster with the conversion instruction, the BF16 one 3 % faster
+// without it.
+template <bool BF>
+__device__ __forceinline__ int32_t floor_of(float t) {
+  if constexpr (BF) return floor_small(t);
+  else return __float2int_rd(t);
+}
+template <bool BF>
+__device__ __forceinline__ float int_to_float(int32_t x) {
+  if constexpr (BF) return small_int_to_float(x);
+  else return (float)x;
+}
+
+template <int DT, bool BF>
 __device__ __forceinline__ int32_t round_clamp(float a) {
   if constexpr (DT == 0) {
     // u8: half away from zero equals floor(a + 1/2) for a >= 0; a < 0 clamps to 0
-    const int32_t v = __float2int_rd(a + 0.5f);
+    const int32_t v = floor_of<BF>(a + 0.5f);
     return min(max(v, 0), 255);
   } else {
-    const int32_t m = __float2int_rd(fabsf(a) + 0.5f);
+    const int32_t m = floor_of<BF>(fabsf(a) + 0.5f);
     return min(max(a < 0.f ? -m : m, -255), 255);
   }
 }
@@ -102,7 +129,7 @@ __global__ void __launch_bounds__(128) dct_codec_kernel(const PlaneDesc P, const
 #pragma unroll
         for (int k = 0; k < 8; ++k) unpack_row<DT>(rw, k, xi + 8 * k);
 #pragma unroll
-        for (int q = 0; q < 64; ++q) x[q] = (float)(int32_t)xi[q];
+        for (int q = 0; q < 64; ++q) x[q] = int_to_float<BF>((int32_t)xi[q]);
       }
       // rows: t[k][j] = sum_l x[k][l] C[j][l], for the needed columns j
       float t[64];
@@ -201,9 +228,9 @@ __global__ void __launch_bounds__(128) dct_codec_kernel(const PlaneDesc P, const
         }
 #pragma unroll
         for (int l = 0; l < 8; ++l) {
-          const int32_t v = round_clamp<DT>(xr[l]);
+          const int32_t v = round_clamp<DT, BF>(xr[l]);
           outp[8 * k + l] = v;
-          const int32_t d = (int32_t)x[8 * k + l] - v;
+          const int32_t d = floor_of<BF>(x[8 * k + l]) - v;  // x holds exact integers
           const bool valid = full || ((by * 8 + k) < P.H && (bx * 8 + l) < P.W);
           s += valid ? (uint32_t)(d * d) : 0u;
         }
