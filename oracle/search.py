@@ -177,40 +177,56 @@ def candidate_block(P: tuple, N: int, start: int, stop: int) -> np.ndarray:
 
 
 def abm_approx_n(N: int, order, P: tuple, tie: str = "small", fixed=None,
-                 chunk: int = 1 << 22):
+                 chunk: int = 1 << 22, partial: bool = False):
     """Greedy search for blocklength N over P^N for the row order ``order``
     (0-based rows of the N-point DCT), with ``fixed`` = {row: vector} preset.
     Returns the N x N int64 matrix (rows not in ``order`` or ``fixed`` stay
-    zero), or None when a row has no orthogonal candidate left."""
+    zero), or None when a row has no orthogonal candidate left.  With
+    ``partial`` it returns (T, complete) instead: on a dead end T holds the
+    rows chosen before it and complete is False.
+
+    The candidates still allowed (nonzero, orthogonal to every preset and to
+    every row chosen so far) are kept as one boolean per candidate and
+    narrowed by each new row before the next row's cosines are taken, as in
+    the 8-point search above.  The candidate vectors are enumerated once per
+    call (int8, in chunks)."""
     C = dct_matrix(N)
     total = len(P) ** N
     T = np.zeros((N, N), dtype=np.int64)
-    chosen = []
+    blocks = [(s, candidate_block(P, N, s, min(total, s + chunk)))
+              for s in range(0, total, chunk)]
+    allowed = np.ones(total, dtype=bool)
+    pending = []  # rows whose orthogonality is not yet applied to `allowed`
     for row, vec in (fixed or {}).items():
         T[row] = vec
-        chosen.append(np.asarray(vec, dtype=np.int64))
+        pending.append(np.asarray(vec, dtype=np.int64))
     for row in order:
-        cos_all = np.full(total, -np.inf)
-        norm2_all = np.zeros(total, dtype=np.int64)
-        for s in range(0, total, chunk):
-            e = min(total, s + chunk)
-            D = candidate_block(P, N, s, e).astype(np.int64)
+        best_cos, best_idx, best_n2 = [], [], []
+        for s, Db in blocks:
+            idx = np.nonzero(allowed[s:s + len(Db)])[0]
+            D = Db[idx].astype(np.int64)
+            keep = np.einsum("ij,ij->i", D, D) > 0
+            for t in pending:
+                keep &= (D @ t) == 0
+            allowed[s + idx[~keep]] = False
+            idx, D = idx[keep], D[keep]
             n2 = np.einsum("ij,ij->i", D, D)
-            ok = n2 > 0
-            for t in chosen:
-                ok &= (D @ t) == 0
-            cos = np.full(e - s, -np.inf)
-            cos[ok] = (D[ok].astype(np.float64) @ C[row]) / np.sqrt(n2[ok])
-            cos_all[s:e] = cos
-            norm2_all[s:e] = n2
+            best_cos.append((D.astype(np.float64) @ C[row]) / np.sqrt(n2))
+            best_idx.append(s + idx)
+            best_n2.append(n2)
+        pending = []
+        cos_all = np.concatenate(best_cos)
+        if cos_all.size == 0:
+            return (T, False) if partial else None
+        idx_all = np.concatenate(best_idx)
+        n2_all = np.concatenate(best_n2)
         best = cos_all.max()
-        if not np.isfinite(best):
-            return None
-        ties = np.nonzero(cos_all >= best - TIE_TOL)[0]
-        if len(ties) > 1:
-            n2 = norm2_all[ties]
-            ties = ties[n2 == (n2.min() if tie == "small" else n2.max())]
-        v = candidate_block(P, N, int(ties[0]), int(ties[0]) + 1)[0].astype(np.int64)
+        sel = np.nonzero(cos_all >= best - TIE_TOL)[0]
+        if len(sel) > 1:
+            n2 = n2_all[sel]
+            sel = sel[n2 == (n2.min() if tie == "small" else n2.max())]
+        first = int(idx_all[sel].min())  # the first tied candidate of the enumeration
+        v = candidate_block(P, N, first, first + 1)[0].astype(np.int64)
         T[row] = v
-        chosen.append(v)
-    return T
+        pending.append(v)
+    return (T, True) if partial else T

@@ -126,6 +126,32 @@ def test_table6_circular(name):
     assert round(got["dmod"], 4) == pytest.approx(dmod, abs=1e-9)
 
 
+def test_mean_circular_difference_closed_forms_and_brute_force():
+    """D-bar of §4.2: the mean over all 64 pairs (i, j) of the circular
+    distance pi - |pi - |theta_ci - theta_tj|| (Table 6 prints only D_mod).
+    Pinned by closed forms, by its relation to the pinned D_mod (the double
+    sum is the mean of D_mod over the 8 cyclic shifts of the second angle
+    set) and by a pure-Python double loop."""
+    import math
+
+    for a, b in [(0.0, math.pi), (0.3, 0.3), (0.1, 2 * math.pi - 0.1), (1.0, 2.5)]:
+        want = min(abs(a - b), 2 * math.pi - abs(a - b))  # shorter arc between the angles
+        got = ms.mean_circular_difference(np.array([a]), np.array([b]))
+        assert got == pytest.approx(want, abs=1e-15)
+    h = np.array([0.0, math.pi / 2])  # pairs 0, pi/2, pi/2, 0
+    assert ms.mean_circular_difference(h, h) == pytest.approx(math.pi / 4, abs=1e-15)
+    th_c = ms.row_angles_to_e1(M.dct_matrix())
+    for name in ("T1", "T2", "RDCT", "T4", "T6"):
+        th_t = ms.row_angles_to_e1(M.NAMED[name])
+        got = ms.mean_circular_difference(th_c, th_t)
+        shifts = [ms.mean_circular_difference_mod(th_c, np.roll(th_t, k)) for k in range(8)]
+        assert got == pytest.approx(sum(shifts) / 8, abs=1e-14)
+        loop = math.fsum(math.pi - abs(math.pi - abs(a - b)) for a in th_c for b in th_t) / 64
+        assert got == pytest.approx(loop, abs=1e-14)
+        assert got == pytest.approx(ms.mean_circular_difference(th_t, th_c), abs=1e-15)
+        assert 0.0 <= got <= math.pi
+
+
 def test_orthogonal_cg_equals_unified_cg():
     Ch = M.approximation(M.T1)
     assert ms.coding_gain(Ch) == pytest.approx(ms.unified_coding_gain(Ch), abs=1e-12)
@@ -454,9 +480,10 @@ def test_search_any_N_reduces_to_the_8_point_search(P, tie):
         assert (a is None and b is None) or np.array_equal(a, b), order
 
 
-def _brute_force_search(N, order, P, tie):
+def _brute_force_search(N, order, P, tie, partial=False):
     """Pure-Python restatement: every candidate of P^N in lexicographic order
-    over sorted(P), cosines with math.fsum, the same tie rules."""
+    over sorted(P), cosines with math.fsum, the same tie rules.  With
+    ``partial``: (rows chosen before a dead end, complete flag)."""
     import itertools
     import math
 
@@ -467,7 +494,7 @@ def _brute_force_search(N, order, P, tie):
     for row in order:
         ok = [d for d in cands if all(sum(a * b for a, b in zip(d, t)) == 0 for t in chosen)]
         if not ok:
-            return None
+            return (np.array(T, dtype=np.int64), False) if partial else None
         cos = [math.fsum(C[row][j] * d[j] for j in range(N)) / math.sqrt(sum(v * v for v in d))
                for d in ok]
         best = max(cos)
@@ -477,7 +504,7 @@ def _brute_force_search(N, order, P, tie):
         pick = [d for d, n in zip(ties, n2) if n == want][0]
         T[row] = list(pick)
         chosen.append(pick)
-    return np.array(T, dtype=np.int64)
+    return (np.array(T, dtype=np.int64), True) if partial else np.array(T, dtype=np.int64)
 
 
 @pytest.mark.parametrize("N,P", [(4, S.P1), (4, S.P2), (5, S.P1)])
@@ -489,6 +516,21 @@ def test_search_any_N_matches_brute_force_on_every_order(N, P):
             want = _brute_force_search(N, order, P, tie)
             got = S.abm_approx_n(N, order, P, tie)
             assert (want is None and got is None) or np.array_equal(got, want), (order, tie)
+
+
+@pytest.mark.parametrize("N,P", [(5, S.P1), (5, S.P2)])
+def test_search_any_N_partial_result_on_dead_ends(N, P):
+    """The (T, complete) form: on a dead end the rows chosen before it are
+    returned; the brute force gives the same rows and the same flag."""
+    import itertools
+
+    dead = 0
+    for order in itertools.permutations(range(N)):
+        want, wc = _brute_force_search(N, order, P, "small", partial=True)
+        got, gc = S.abm_approx_n(N, order, P, "small", partial=True)
+        assert gc == wc and np.array_equal(got, want), order
+        dead += not wc
+    assert dead == 120  # every order of N = 5 dead-ends: the case is exercised
 
 
 # ---- §6.2: the 16- and 32-point matrices of the JAM recursion ---------------------------
