@@ -17,11 +17,16 @@ With N > 1 (torchrun) every rank runs its own replica of the workload
 line.  ``--impl reference`` times the CPU oracle on host cores instead.
 
 Besides the step, the default run reports on the same images: ``e2e`` (the
-host-buffer call with its copies), ``ssim`` (mean SSIM of original vs
-reconstruction), ``jam`` (16x16 and 32x32 blocks with the JAM matrices),
-``dct`` (the exact-DCT comparison codec, FP32 and BF16) and ``search`` (the
-greedy angle search, N = 16 and 12); ``--no-e2e``, ``--no-ssim``,
-``--no-jam``, ``--no-dct`` and ``--no-search`` skip them.
+host-buffer call with its copies; ``e2e_recon`` also returns every
+reconstruction), ``ssim`` (mean SSIM of original vs reconstruction), ``jam``
+(16x16 and 32x32 blocks with the JAM matrices), ``dct`` (the exact-DCT
+comparison codec, FP32 and BF16) and ``search`` (the greedy angle search,
+N = 16 and 12); ``configs`` times the other workloads (single_512,
+sweep_64x512, ragged_2000, video_600x1080p) each on its own, with its own
+oracle parity sample; ``parity`` checks the timed run's per-image SSE against
+the oracle on the cpu_baseline sample; ``cpu_baseline`` times the oracle on
+all host cores and on one.  ``--no-e2e``, ``--no-ssim``, ``--no-jam``,
+``--no-dct``, ``--no-search`` and ``--no-configs`` skip them.
 """
 from __future__ import annotations
 
@@ -67,8 +72,13 @@ def parse():
                     help="skip the angle-search timing (N = 16 and N = 12, P = {-1, 0, 1})")
     ap.add_argument("--no-ssim", action="store_true",
                     help="skip the MSSIM measurement (originals vs reconstructions)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (single_512, sweep_64x512, ragged_2000, "
+                         "video_600x1080p)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
-                    help="CPU-oracle sample budget (seconds of host work)")
+                    help="CPU-oracle sample budget (seconds of host work, all cores)")
+    ap.add_argument("--cpu-seconds-single", type=float, default=4.0,
+                    help="CPU-oracle sample budget on one core")
     return ap.parse_args()
 
 
@@ -181,18 +191,22 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(blocks: int):
-    """DRAM bytes per launch of the fused codec from the committed ncu summary,
-    scaled to `blocks`; None when the kernel sources changed since the capture."""
+def profiled_traffic(images: int):
+    """DRAM bytes (read + write) of one launch of the fused codec on the bench
+    workload, from the committed ncu summary of a capture of that same launch
+    (1024 images); None when the kernel sources changed since the capture or
+    the workload differs."""
     import glob
     import re
 
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "codec_u8_tma_kernel_*_full.md"))):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "codec_u8_tma_kernel_*.md"))):
         text = open(path).read()
         m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-        m_t = re.search(r"traffic_bytes_per_block:\s*([0-9.]+)", text)
-        if m_h and m_t and m_h.group(1) == kernel_source_hash():
-            return float(m_t.group(1)) * blocks, os.path.basename(path)
+        m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9.]+)", text)
+        m_i = re.search(r"traffic_images:\s*([0-9]+)", text)
+        if (m_h and m_t and m_i and m_h.group(1) == kernel_source_hash()
+                and int(m_i.group(1)) == images):
+            return float(m_t.group(1)), os.path.basename(path)
     return None, None
 
 
@@ -211,6 +225,44 @@ def measured_peaks():
         return float(p["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+# Nominal HBM3e bandwidth of one GB300 (8 stacks, 7.9 TB/s), for the fraction
+# beside the measured copy bandwidth.
+NOMINAL_HBM_GBS = 7900.0
+
+
+def device_sms() -> int:
+    import torch
+
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def hbm_figures(algo_bytes: float, ms: float) -> dict:
+    """Achieved bandwidth of `algo_bytes` moved in `ms`, against the measured
+    copy bandwidth and the nominal HBM3e peak."""
+    peak, kind = measured_peaks()
+    gbs = algo_bytes / (ms / 1e3) / 1e9
+    return {"hbm_gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_kind": kind,
+            "frac_of_nominal": gbs / NOMINAL_HBM_GBS, "nominal_peak": NOMINAL_HBM_GBS}
+
+
+def time_launches(fn, stream, steps: int, warmup: int = 3) -> float:
+    """Mean ms per call of `fn()` over `steps` calls, CUDA events on `stream`
+    (the launching stream), after `warmup` untimed calls."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
 
 
 # ---- workloads --------------------------------------------------------------------------------
@@ -318,9 +370,10 @@ def time_ours(args, dist, out):
     kernel_ms = statistics.mean(kev[k].elapsed_time(kev[k + 1]) for k in range(args.steps))
     peak, peak_kind = measured_peaks()
     achieved = algo_bytes / (kernel_ms / 1e3) / 1e9
-    traffic, traffic_src = (profiled_traffic(wl.blocks)
+    traffic, traffic_src = (profiled_traffic(wl.desc["images"])
                             if args.workload == "batch_1024x1024" and args.transform == "T1"
                             else (None, None))
+    wl.sse_host = sse.cpu().numpy()  # the timed configuration's SSE (parity below)
     out.update({
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
@@ -334,6 +387,8 @@ def time_ours(args, dist, out):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "peak_kind": peak_kind,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                     "nominal_peak": NOMINAL_HBM_GBS,
                      "algo_bytes_per_launch": algo_bytes, "kernel_ms": kernel_ms},
         "clocks": clk,
         "gpu_launches": plan.kernel_count() * args.steps,
@@ -378,6 +433,38 @@ def time_ours(args, dist, out):
                       "h2d_bytes_per_step": int(wl.in_bytes), "d2h_bytes_per_step": 16 * n,
                       "steps": ke, "call": "tdct_codec_error_batched_host",
                       "reconstruction_returned": False}
+        # The same call returning every reconstruction to pinned host memory
+        # (the device-timed step writes them to HBM): 1 GiB back per step.
+        rec_bufs = [torch.empty_like(hb).pin_memory() for hb in host_bufs]
+        rows_r = []
+        for row, (pl, _) in zip(rows, wl.planes):
+            k = next(k for k, st in enumerate(wl.storage)
+                     if st.data_ptr() <= pl.data_ptr() < st.data_ptr() + st.numel() * st.element_size())
+            rp = rec_bufs[k].data_ptr() + (row[0] - host_bufs[k].data_ptr())
+            rows_r.append(row[:6] + (rp, row[1]))
+        planes_r = P.make_planes_raw(rows_r)
+
+        def e2e_recon_step():
+            P.tdct_codec_error_batched_host(planes_r, sse_h, psnr_h, stream=stream, **Tn)
+
+        for _ in range(2):
+            e2e_recon_step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_recon_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        r_ms = dist.max(e0.elapsed_time(e1))
+        out["e2e_recon"] = {"value": blocks_all * ke / (r_ms / 1e3), "unit": UNIT,
+                            "h2d_bytes_per_step": int(wl.in_bytes),
+                            "d2h_bytes_per_step": int(wl.out_bytes) + 16 * n, "steps": ke,
+                            "call": "tdct_codec_error_batched_host",
+                            "reconstruction_returned": True}
+        del rec_bufs, host_bufs
     # MSSIM of every image against its reconstruction (the third figure of
     # merit of the paper's image experiment), timed separately: FP32 work on
     # the CUDA cores, reported against the FP32 FMA peak from unit counts and
@@ -401,13 +488,13 @@ def time_ours(args, dist, out):
         windows = sum((pl.shape[0] - 10) * (pl.shape[1] - 10) for pl, _ in u8_planes)
         flops = 245.0 * windows  # 5 maps x 11 taps x 2 passes x 2 FLOP + the index
         sm_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        peak = device_sms() * 128 * 2 * sm_mhz * 1e6 / 1e12
         out["ssim"] = {"value": windows / (ms / 1e3), "unit": "windows/s", "ms": ms,
                        "blocks_per_s": wl.blocks / (ms / 1e3), "mean_mssim": mssim.mean().item(),
                        "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12,
                                     "peak": peak, "unit": "TFLOP/s",
                                     "frac": flops / (ms / 1e3) / 1e12 / peak,
-                                    "peak_kind": "FP32 FMA lanes x max SM clock"}}
+                                    "peak_kind": "FP32 FMA lanes (SMs x 128) x 2 x max SM clock"}}
     # The codec with 16x16 and 32x32 blocks and the JAM matrices of §6.2, on
     # the same images (the batch as one tall plane: 1024 is a multiple of the
     # block sides, so no block straddles two images), reconstruction written.
@@ -462,6 +549,119 @@ def time_ours(args, dist, out):
         out["dct"] = dct
     plan.close()
     return wl
+
+
+def oracle_parity(samples, sse_gpu, transform: str = "T1") -> dict:
+    """Compare the oracle's SSE of each sampled plane with the GPU's.
+    `samples`: (index into sse_gpu, host plane, r); one thread per core."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import codec as oc
+
+    oc.lib()
+    T = oracle_matrix(transform)
+
+    def one(item):
+        i, img, r = item
+        return i, int(oc.codec_plane(img, T, r, want_recon=False)[0])
+
+    with ThreadPoolExecutor(max(1, min(os.cpu_count() or 1, len(samples)))) as ex:
+        got = list(ex.map(one, samples))
+    bad = [i for i, want in got if int(sse_gpu[i]) != want]
+    return {"planes": len(got), "mismatches": len(bad), "first_mismatch": bad[0] if bad else None,
+            "check": "per-plane SSE of the timed run vs the C oracle (int64 definition)"}
+
+
+def time_configs(args, stream) -> dict:
+    """The other workloads of the paper's experiments, each timed on its own
+    (plan replays, CUDA events on the launching stream, inputs resident in
+    HBM) and checked against the oracle on a sample of its planes:
+    single_512 (one 512x512 image, r = 10; launch-bound), sweep_64x512 (64
+    images x every r = 1..64, SSE per (image, r)), ragged_2000 (2000 images
+    of random sizes, r in {4, 8, 16, 32}) and video_600x1080p (1797 int16
+    residual planes, r = 16 / 8)."""
+    import numpy as np
+    import torch
+
+    import paper_1808_02950_gb300 as P
+    from paper_1808_02950_gb300 import synth
+
+    dev = "cuda"
+    steps = max(5, min(args.steps, 20))
+    res = {}
+
+    def plan_entry(planes, n, samples_fn, blocks, algo_bytes, unit_scale=1, unit=UNIT,
+                   bound="hbm"):
+        plan = P.tdct_plan_create(planes)
+        sse = torch.zeros(n, dtype=torch.int64, device=dev)
+        psnr = torch.zeros(n, dtype=torch.float64, device=dev)
+        ms = time_launches(lambda: plan.launch(sse, psnr, stream), stream, steps)
+        torch.cuda.synchronize()
+        entry = {"value": blocks * unit_scale / (ms / 1e3), "unit": unit, "ms": ms,
+                 "blocks": blocks, "algo_bytes": algo_bytes, "bound": bound,
+                 **hbm_figures(algo_bytes, ms), "plan": plan.config(),
+                 "launches_per_step": plan.kernel_count(),
+                 "groups": len(plan.groups())}
+        entry["parity"] = oracle_parity(samples_fn(), sse.cpu().numpy())
+        plan.close()
+        return entry
+
+    # config 1: one 512x512 u8 image, r = 10 (4096 blocks: launch-bound)
+    img, r = synth.single_512(dev)
+    rec = torch.empty_like(img)
+    res["single_512"] = plan_entry(
+        P.make_planes([img], [r], [rec]), 1, lambda: [(0, img.cpu().numpy(), r)], 4096,
+        2 * img.numel() + 16, bound="launch")
+    res["single_512"]["r"] = r
+    del img, rec
+
+    # config 2: 64 images x r = 1..64, SSE per (image, r), one plane per pair
+    imgs, _ = synth.sweep_64x512(dev)
+    planes = [imgs[i] for i in range(64) for _ in range(64)]
+    rs = [r for _ in range(64) for r in range(1, 65)]
+    host = imgs.cpu().numpy()
+    sample_imgs = (0, 21, 42, 63)
+    e = plan_entry(P.make_planes(planes, rs), len(planes),
+                   lambda: [(64 * i + r - 1, host[i], r) for i in sample_imgs for r in range(1, 65)],
+                   64 * 4096, 64 * 64 * 512 * 512 + 16 * 4096, unit_scale=64, unit="block*r/s",
+                   bound="alu")
+    e["method"] = "one plane per (image, r): each image read once per r (L2-resident)"
+    res["sweep_64x512"] = e
+    del imgs, planes
+
+    # config 4: 2000 u8 images of random sizes, r drawn per image
+    buf, offs, H, W, rr = synth.ragged_2000(dev)
+    rbuf = torch.empty_like(buf)
+    views, rviews = [], []
+    for i in range(len(offs)):
+        o, h, w = int(offs[i]), int(H[i]), int(W[i])
+        views.append(buf[o: o + h * w].view(h, w))
+        rviews.append(rbuf[o: o + h * w].view(h, w))
+    npx = int((H * W).sum())
+    idx = list(range(0, len(offs), len(offs) // 32))[:32]
+    res["ragged_2000"] = plan_entry(
+        P.make_planes(views, [int(v) for v in rr], rviews), len(offs),
+        lambda: [(i, views[i].cpu().numpy(), int(rr[i])) for i in idx],
+        int(((H + 7) // 8 * ((W + 7) // 8)).sum()), 2 * npx + 16 * len(offs))
+    del buf, rbuf, views, rviews
+
+    # config 5: 599 residual frames of 1080p 4:2:0 video (int16), r = 16 (Y) / 8 (U, V)
+    Y, U, V = synth.video_600x1080p(dev)
+    planes, rs = [], []
+    for t in range(Y.shape[0]):
+        planes += [Y[t], U[t], V[t]]
+        rs += [16, 8, 8]
+    recs = [torch.empty_like(p) for p in planes]
+    nbytes = sum(p.numel() * p.element_size() for p in planes)
+    blocks = sum(((p.shape[0] + 7) // 8) * ((p.shape[1] + 7) // 8) for p in planes)
+    idx = list(range(0, len(planes), 61))
+    res["video_600x1080p"] = plan_entry(
+        P.make_planes(planes, rs, recs), len(planes),
+        lambda: [(i, planes[i].cpu().numpy(), rs[i]) for i in idx],
+        blocks, 2 * nbytes + 16 * len(planes))
+    del Y, U, V, planes, recs
+    torch.cuda.empty_cache()
+    return res
 
 
 def jam_matrix(B: int):
@@ -519,9 +719,11 @@ def oracle_matrix(name: str):
     return (2 * M.T_LO).astype("int64") if name == "LOx2" else M.NAMED[name]
 
 
-def cpu_oracle_rate(planes_host, budget_s: float, transform: str = "T1"):
-    """Run the oracle over host planes with one thread per core until the
-    budget is spent; returns (blocks/s, blocks done, threads, planes done)."""
+def cpu_oracle_rate(planes_host, budget_s: float, transform: str = "T1", threads: int = 0,
+                    sses: dict | None = None):
+    """Run the oracle over host planes with `threads` threads (0: one per
+    core) until the budget is spent; returns (blocks/s, blocks done, threads,
+    planes done).  `sses`, if given, receives {sample position: SSE}."""
     from concurrent.futures import ThreadPoolExecutor
 
     from oracle import codec as oc
@@ -544,13 +746,15 @@ def cpu_oracle_rate(planes_host, budget_s: float, transform: str = "T1"):
                 i = idx[0]
                 idx[0] += 1
             img, r = planes_host[i]
-            oc.codec_plane(img, T, r)
+            got = oc.codec_plane(img, T, r)[0]
             nb = ((img.shape[0] + 7) // 8) * ((img.shape[1] + 7) // 8)
             with lock:
                 done_blocks += nb
                 done_planes += 1
+                if sses is not None:
+                    sses[i] = int(got)
 
-    threads = max(1, min(cores, len(planes_host)))
+    threads = max(1, min(threads or cores, len(planes_host)))
     with ThreadPoolExecutor(threads) as ex:
         for f in [ex.submit(worker) for _ in range(threads)]:
             f.result()
@@ -558,11 +762,14 @@ def cpu_oracle_rate(planes_host, budget_s: float, transform: str = "T1"):
     return done_blocks / dt, done_blocks, threads, done_planes
 
 
+def sample_indices(n: int, max_planes: int) -> list:
+    return list(range(0, n, max(1, n // max_planes)))[:max_planes]
+
+
 def host_sample(wl, max_planes: int):
     """Copy an evenly spaced sample of the workload's planes to host memory."""
-    n = len(wl.planes)
-    step = max(1, n // max_planes)
-    return [(wl.planes[i][0].cpu().numpy(), wl.planes[i][1]) for i in range(0, n, step)][:max_planes]
+    return [(wl.planes[i][0].cpu().numpy(), wl.planes[i][1])
+            for i in sample_indices(len(wl.planes), max_planes)]
 
 
 def main():
@@ -575,14 +782,33 @@ def main():
     dist = Dist(backend)
     out = {}
     wl = time_ours(args, dist, out)
+    if dist.rank == 0 and dist.world == 1 and not args.no_configs and \
+            args.workload == "batch_1024x1024" and args.transform == "T1":
+        import torch
+
+        out["configs"] = time_configs(args, torch.cuda.current_stream())
     if dist.rank == 0 and not args.no_search:
         out["search"] = time_search(args.no_cpu_baseline or dist.world > 1)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        idx = sample_indices(len(wl.planes), 256)
         sample = host_sample(wl, 256)
-        rate, nb, cores, npl = cpu_oracle_rate(sample, args.cpu_seconds, args.transform)
+        sses = {}
+        rate, nb, cores, npl = cpu_oracle_rate(sample, args.cpu_seconds, args.transform,
+                                               sses=sses)
+        rate1, nb1, _, npl1 = cpu_oracle_rate(sample, args.cpu_seconds_single, args.transform,
+                                              threads=1)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{npl} of {len(wl.planes)} planes ({nb} blocks), "
-                                         f"C oracle (int64 definition), one thread per core"}
+                                         f"C oracle (int64 definition), one thread per core",
+                               "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                                               "sample": f"{npl1} planes ({nb1} blocks)"}}
+        # the bit-exactness claim, checked on the run that was timed: the
+        # oracle's SSE of every sampled plane against the timed plan's SSE
+        bad = [idx[k] for k, v in sses.items() if int(wl.sse_host[idx[k]]) != v]
+        out["parity"] = {"planes": len(sses), "mismatches": len(bad),
+                         "first_mismatch": bad[0] if bad else None,
+                         "check": "per-plane SSE of the timed run vs the C oracle (int64 "
+                                  "definition), planes of the cpu_baseline sample"}
     if dist.rank == 0:
         print(json.dumps(out))
     dist.close()

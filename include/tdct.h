@@ -177,7 +177,9 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
  *   per device, with that device current); make that first call before any
  *   stream capture.  Every call rewrites the shared array: calls whose work
  *   overlaps on the GPU (for example on two streams) race on it and must be
- *   serialised by the caller.
+ *   serialised by the caller.  Calls from several host threads enqueue their
+ *   table copy and kernels under one library lock, so their enqueues never
+ *   interleave; the GPU-side rule above still applies.
  */
 #define TDCT_NOALLOC_MAX_PLANES 2048
 int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, const int8_t T[64],
@@ -383,6 +385,21 @@ int tdct_debug_inject_wait_timeout(int enable);
  * it; the test suite uses a small cap to run the fallback scan.
  */
 int tdct_debug_search_hit_cap(int cap);
+
+/*
+ * tdct_shutdown -- release what the library owns (the workspace convention
+ * of the boundary: caller-owned buffers everywhere, library-owned resources
+ * released here).  Waits for and destroys the per-device transfer streams of
+ * tdct_codec_error_batched_host.  The fixed device arrays (status word,
+ * tensor-core weight tables, the table of tdct_codec_error_batched_noalloc)
+ * are part of the library's device image and go with the CUDA context; plans
+ * belong to the caller (tdct_plan_destroy).  Call it when no call of the
+ * library is in flight; afterwards the library stays usable and re-creates
+ * the streams on demand.  Calling it again is harmless.  The current device
+ * is restored.  Errors: TDCT_ECUDA (the first failing CUDA call; the streams
+ * are released regardless).
+ */
+int tdct_shutdown(void);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* tdct_last_error(void);

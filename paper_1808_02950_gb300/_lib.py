@@ -40,7 +40,7 @@ EXPORTS = (
     "tdct_plan_groups",
     "tdct_plan_destroy",
     "tdct_dct_codec_error", "tdct_sync_status", "tdct_debug_inject_wait_timeout",
-    "tdct_debug_search_hit_cap",
+    "tdct_debug_search_hit_cap", "tdct_shutdown",
     "tdct_last_error", "tdct_version",
 )
 
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_plan_destroy.restype = None
     L.tdct_dct_codec_error.argtypes = [vp, i64, i32, i32, i32, i32, i32, vp, vp, i64, vp, vp, vp]
     L.tdct_sync_status.argtypes = [vp]
+    L.tdct_shutdown.argtypes = []
     L.tdct_debug_inject_wait_timeout.argtypes = [i32]
     L.tdct_debug_search_hit_cap.argtypes = [i32]
     L.tdct_last_error.restype = ctypes.c_char_p
@@ -361,3 +362,9 @@ def tdct_debug_search_hit_cap(cap: int = -1) -> None:
 
 def tdct_sync_status(stream=None) -> None:
     _check(load().tdct_sync_status(_stream(stream)))
+
+
+def tdct_shutdown() -> None:
+    """Release the library-owned resources (transfer streams); the library
+    stays usable afterwards."""
+    _check(load().tdct_shutdown())

@@ -833,6 +833,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 namespace {
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[256] = {};
+// Held by each no-alloc call from its first table copy to its last launch,
+// so that calls from several host threads enqueue their table and their
+// kernels as one sequence (the table is shared).
+std::mutex g_noalloc_call_mu;
 
 // Device address of g_noalloc_scratch on the current device (looked up once
 // per device; the host-side symbol is not a device address).
@@ -977,6 +981,7 @@ int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, cons
   PlaneDesc* d_descs = static_cast<PlaneDesc*>(scratch);
   int64_t* d_npix = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + kNoAllocDescBytes);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> call_lock(g_noalloc_call_mu);
   cudaError_t e = cudaMemcpyAsync(d_descs, descs.data(), sizeof(PlaneDesc) * descs.size(),
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -1437,6 +1442,28 @@ int tdct_debug_inject_wait_timeout(int enable) {
 int tdct_debug_search_hit_cap(int cap) {
   g_search_hit_cap.store(cap >= 0 && cap <= kSearchHitCap ? cap : kSearchHitCap);
   return TDCT_OK;
+}
+
+int tdct_shutdown(void) {
+  int cur = 0;
+  const bool have_cur = cudaGetDevice(&cur) == cudaSuccess;
+  cudaError_t first = cudaSuccess;
+  std::lock_guard<std::mutex> lock(g_host_mu);
+  for (int dev = 0; dev < 256; ++dev) {
+    HostStreams& hs = g_host_streams[dev];
+    if (!hs.h2d && !hs.d2h) continue;
+    cudaError_t e = cudaSetDevice(dev);
+    for (cudaStream_t* st : {&hs.h2d, &hs.d2h}) {
+      if (!*st) continue;
+      if (e == cudaSuccess) e = cudaStreamSynchronize(*st);
+      const cudaError_t ed = cudaStreamDestroy(*st);
+      if (e == cudaSuccess) e = ed;
+      *st = nullptr;
+    }
+    if (first == cudaSuccess) first = e;
+  }
+  if (have_cur) cudaSetDevice(cur);
+  return first == cudaSuccess ? TDCT_OK : cuda_fail(first, "tdct_shutdown");
 }
 
 int tdct_sync_status(tdct_stream_t stream) {

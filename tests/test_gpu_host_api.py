@@ -78,3 +78,20 @@ def test_host_batch_images_large_and_generic_T():
         for i in (0, 37, 63):
             assert int(sse_h[i]) == oc.codec_plane(hosts[i], M.T1 if T is None else T, 16,
                                                    want_recon=False)[0]
+
+
+def test_shutdown_releases_streams_and_library_stays_usable():
+    """tdct_shutdown destroys the library-owned transfer streams; a later
+    host-buffer call re-creates them and still matches the oracle, and a
+    second shutdown is harmless."""
+    rng = np.random.default_rng(21)
+    hosts, tens = host_planes(rng, SHAPES[:4], pin=True)
+    rs = [10, 16, 8, 28]
+    for _ in range(2):
+        sse = torch.full((4,), -1, dtype=torch.int64).pin_memory()
+        P.tdct_codec_error_batched_host(P.make_planes(tens, rs), sse)
+        torch.cuda.synchronize()
+        for i, (h, r) in enumerate(zip(hosts, rs)):
+            assert int(sse[i]) == oc.codec_plane(h, M.T1, r, want_recon=False)[0]
+        P.tdct_shutdown()
+    P.tdct_shutdown()
