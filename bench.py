@@ -615,19 +615,55 @@ def time_configs(args, stream) -> dict:
     res["single_512"]["r"] = r
     del img, rec
 
-    # config 2: 64 images x r = 1..64, SSE per (image, r), one plane per pair
+    # config 2: 64 images x r = 1..64, SSE per (image, r): the single-read
+    # sweep (T1, and the exact DCT in FP32), with the per-r-plane batch of
+    # the fused codec (each image read once per r) as the comparison
     imgs, _ = synth.sweep_64x512(dev)
-    planes = [imgs[i] for i in range(64) for _ in range(64)]
-    rs = [r for _ in range(64) for r in range(1, 65)]
+    views = [imgs[i] for i in range(64)]
     host = imgs.cpu().numpy()
+    sw_sse = torch.zeros(64 * 64, dtype=torch.int64, device=dev)
+    sw_psnr = torch.zeros(64 * 64, dtype=torch.float64, device=dev)
+    planes_sw = P.make_planes(views, [64] * 64)
+    Tb, nb_ = P._lib._T_n()
+    L = P.load()
+    stream_h = stream.cuda_stream
+
+    def sweep_t1():
+        P._lib._check(L.tdct_sweep_batched(P._lib.ctypes.addressof(planes_sw), 64, Tb, nb_,
+                                           sw_sse.data_ptr(), sw_psnr.data_ptr(), stream_h))
+
+    def sweep_dct():
+        P._lib._check(L.tdct_dct_sweep_batched(P._lib.ctypes.addressof(planes_sw), 64,
+                                               P.TDCT_FP32, sw_sse.data_ptr(),
+                                               sw_psnr.data_ptr(), stream_h))
+
+    block_r = 64 * 4096 * 64
+    ms_t1 = time_launches(sweep_t1, stream, steps)
+    sweep_t1()
+    torch.cuda.synchronize()
+    got = sw_sse.cpu().numpy()
     sample_imgs = (0, 21, 42, 63)
-    e = plan_entry(P.make_planes(planes, rs), len(planes),
-                   lambda: [(64 * i + r - 1, host[i], r) for i in sample_imgs for r in range(1, 65)],
-                   64 * 4096, 64 * 64 * 512 * 512 + 16 * 4096, unit_scale=64, unit="block*r/s",
-                   bound="alu")
-    e["method"] = "one plane per (image, r): each image read once per r (L2-resident)"
-    res["sweep_64x512"] = e
-    del imgs, planes
+    par = oracle_parity([(64 * i + r - 1, host[i], r) for i in sample_imgs for r in range(1, 65)],
+                        got)
+    ms_dct = time_launches(sweep_dct, stream, steps)
+    # the comparison: one plane per (image, r) through the fused codec
+    plan = P.tdct_plan_create(P.make_planes([v for v in views for _ in range(64)],
+                                            [r for _ in range(64) for r in range(1, 65)]))
+    pl_sse = torch.zeros(4096, dtype=torch.int64, device=dev)
+    ms_planes = time_launches(lambda: plan.launch(pl_sse, None, stream), stream, steps)
+    plan.close()
+    sms = device_sms()
+    res["sweep_64x512"] = {
+        "value": block_r / (ms_t1 / 1e3), "unit": "block*r/s", "ms": ms_t1, "blocks": 64 * 4096,
+        "r": "1..64", "bound": "alu", "method": "one read per image, incremental reconstruction "
+        "(tdct_sweep_batched)", "parity": par,
+        "ops_per_block_r": 288, "int_ops_per_s": 288 * block_r / (ms_t1 / 1e3),
+        "issue_peak_ops_per_s": sms * 4 * 32 * 2.07e9,
+        "dct_fp32": {"value": block_r / (ms_dct / 1e3), "unit": "block*r/s", "ms": ms_dct,
+                     "call": "tdct_dct_sweep_batched"},
+        "per_r_planes": {"value": block_r / (ms_planes / 1e3), "unit": "block*r/s",
+                         "ms": ms_planes, "method": "4096 planes (image, r) in one plan"}}
+    del imgs, views
 
     # config 4: 2000 u8 images of random sizes, r drawn per image
     buf, offs, H, W, rr = synth.ragged_2000(dev)

@@ -215,6 +215,40 @@ int tdct_codec_error_batched_host(const tdct_plane* planes, int nplanes, const i
                                   size_t chunk_bytes, tdct_stream_t stream);
 
 /*
+ * tdct_sweep_batched -- the zonal sweep of §6.1: for every plane, the SSE of
+ * the codec with each retention r = 1, 2, ..., 64, from one read of the
+ * plane.  Each block is transformed once (Z = T1 A T1^T) and reconstructed
+ * incrementally, one zig-zag basis image per r; every r's reconstruction
+ * is rounded and clamped exactly as tdct_codec_error does, so entry r is bit
+ * for bit the SSE that tdct_codec_error returns for that r.
+ *   planes    host array of nplanes u8 planes (1 <= nplanes <= 2^20); their
+ *             r fields are not used; recon must be NULL (reconstructions are
+ *             not written)
+ *   T, n      T1 and its squared row norms (TDCT_EUNSUPPORTED for any other
+ *             orthogonal T; TDCT_ENOTORTHO as usual)
+ *   d_sse     output, uint64 [nplanes][64]: d_sse[64 p + r - 1]
+ *   d_psnr    output or NULL, double [nplanes][64], +inf where SSE = 0
+ * Device scratch for the plane table comes from the stream-ordered pool.
+ * Errors: TDCT_EINVAL (arguments, as tdct_codec_error_batched),
+ *         TDCT_EUNSUPPORTED (int16 planes, T != T1), TDCT_ENOMEM, TDCT_ECUDA.
+ */
+int tdct_sweep_batched(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                       const int32_t n[8], uint64_t* d_sse, double* d_psnr,
+                       tdct_stream_t stream);
+
+/*
+ * tdct_dct_sweep_batched -- the same sweep with the exact orthonormal
+ * DCT-II of §2 (the comparison transform of §6.1) in FP32:
+ * x_r = 1/2 + sum_{s < r} Y_s (C_i[k] C_j[l]) accumulated one basis image
+ * per r, floored and clamped to [0, 255].  Close to, not identical with,
+ * the FP64 definition (PSNR within 0.01 dB).
+ *   precision TDCT_FP32 (TDCT_BF16 returns TDCT_EUNSUPPORTED)
+ *   other arguments as tdct_sweep_batched
+ */
+int tdct_dct_sweep_batched(const tdct_plane* planes, int nplanes, int precision,
+                           uint64_t* d_sse, double* d_psnr, tdct_stream_t stream);
+
+/*
  * tdct_codec_error_jam -- the codec of §6.1 with B x B blocks, B = 16 or 32,
  * and the B-point transforms that §6.2 derives from T1 with the JAM
  * recursion (T_(16) and T_(32) as printed there; Ĉ = S T with S from

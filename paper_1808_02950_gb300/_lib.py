@@ -35,7 +35,7 @@ N1 = (8, 18, 20, 18, 8, 18, 20, 18)
 EXPORTS = (
     "tdct_forward", "tdct_zonal_inverse", "tdct_codec_error", "tdct_codec_error_batched",
     "tdct_codec_error_batched_noalloc", "tdct_codec_error_batched_host", "tdct_ssim_batched",
-    "tdct_search", "tdct_codec_error_jam",
+    "tdct_search", "tdct_codec_error_jam", "tdct_sweep_batched", "tdct_dct_sweep_batched",
     "tdct_plan_create", "tdct_plan_launch", "tdct_plan_kernel_count", "tdct_plan_config",
     "tdct_plan_groups",
     "tdct_plan_destroy",
@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tdct_codec_error_batched_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
     L.tdct_codec_error_batched_host.argtypes = [vp, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.tdct_ssim_batched.argtypes = [vp, i32, vp, vp]
+    L.tdct_sweep_batched.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.tdct_dct_sweep_batched.argtypes = [vp, i32, i32, vp, vp, vp]
     L.tdct_search.argtypes = [i32, vp, i32, vp, i32, vp, vp, i32, i32, vp, vp, vp]
     L.tdct_codec_error_jam.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp, i32, vp, i64, vp, vp,
                                        vp]
@@ -235,6 +237,22 @@ def tdct_codec_error_batched_host(planes, sse, psnr=None, T=None, n=None, chunk_
     _check(load().tdct_codec_error_batched_host(ctypes.addressof(planes), len(planes), tb, nb,
                                                 _ptr(sse), _ptr(psnr), int(chunk_bytes),
                                                 _stream(stream)))
+
+
+def tdct_sweep_batched(imgs, sse, psnr=None, T=None, n=None, stream=None) -> None:
+    """SSE (and PSNR) of every u8 plane of ``imgs`` for each r = 1..64 into
+    ``sse[64 * p + r - 1]`` (int64 device tensor of 64 * len(imgs))."""
+    planes = make_planes(imgs, [64] * len(imgs))
+    tb, nb = _T_n(T, n)
+    _check(load().tdct_sweep_batched(ctypes.addressof(planes), len(planes), tb, nb, _ptr(sse),
+                                     _ptr(psnr), _stream(stream)))
+
+
+def tdct_dct_sweep_batched(imgs, sse, psnr=None, precision=TDCT_FP32, stream=None) -> None:
+    """The sweep with the exact DCT in FP32 (same layout as tdct_sweep_batched)."""
+    planes = make_planes(imgs, [64] * len(imgs))
+    _check(load().tdct_dct_sweep_batched(ctypes.addressof(planes), len(planes), int(precision),
+                                         _ptr(sse), _ptr(psnr), _stream(stream)))
 
 
 class TdctSsimPlane(ctypes.Structure):

@@ -24,11 +24,13 @@
 #include "../../include/tdct.h"
 #include "tdct_classes.h"
 #include "tdct_dct.h"
+#include "tdct_dct_tc.h"
 #include "tdct_generic.cuh"
 #include "tdct_jam.h"
 #include "tdct_kernels.cuh"
 #include "tdct_search.h"
 #include "tdct_ssim.h"
+#include "tdct_sweep.h"
 #include "tdct_tc.h"
 
 namespace tdct {
@@ -381,6 +383,16 @@ __global__ void psnr_kernel(const unsigned long long* __restrict__ sse,
   const unsigned long long s = sse[i];
   const double np = (double)(npix ? npix[i] : npix_one);
   psnr[i] = s == 0ull ? (double)INFINITY : 10.0 * log10(65025.0 * np / (double)s);
+}
+
+// PSNR of every (plane, r) entry of a sweep: entry e belongs to plane e / 64.
+__global__ void psnr_sweep_kernel(const unsigned long long* __restrict__ sse,
+                                  const int64_t* __restrict__ npix, double* __restrict__ psnr,
+                                  int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const unsigned long long v = sse[e];
+  psnr[e] = v == 0ull ? (double)INFINITY : 10.0 * log10(65025.0 * (double)npix[e / 64] / (double)v);
 }
 
 namespace {
@@ -1425,13 +1437,114 @@ int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dty
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_dct_codec_error memset");
   const PlaneDesc P = make_desc(d_img, pitch, H, W, dtype, r, d_recon, recon_pitch, 0);
-  if ((e = launch_dct_codec(P, precision, d_coef, sse, s)) != cudaSuccess)
-    return cuda_fail(e, "tdct_dct_codec_error launch");
+  // bf16 on u8 planes: the two GEMMs on the tensor cores; otherwise the CUDA cores
+  e = (precision == TDCT_BF16 && dtype == TDCT_U8)
+          ? launch_dct_tc(P, d_coef, status_word(), sse, s)
+          : launch_dct_codec(P, precision, d_coef, sse, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tdct_dct_codec_error launch");
   if (d_psnr) {
     psnr_kernel<<<1, 32, 0, s>>>(sse, nullptr, (int64_t)H * W, d_psnr, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "psnr launch");
   }
   return TDCT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Shared body of the two sweep entry points: validation, the sweep's unit
+// table (32 blocks per unit) in stream-ordered scratch, the kernel, PSNR.
+int sweep_batched(const tdct_plane* planes, int nplanes, bool dct, const float* C,
+                  uint64_t* d_sse, double* d_psnr, cudaStream_t s, const char* who) {
+  if (!planes || nplanes < 1 || nplanes > (1 << 20))
+    return fail(TDCT_EINVAL, "%s: nplanes = %d outside 1..2^20 (or planes is NULL)", who, nplanes);
+  if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
+    return fail(TDCT_EINVAL, "%s: d_sse NULL or not 8-byte aligned", who);
+  if (d_psnr && (reinterpret_cast<uintptr_t>(d_psnr) & 7))
+    return fail(TDCT_EINVAL, "%s: d_psnr not 8-byte aligned", who);
+  std::vector<PlaneDesc> descs(nplanes);
+  std::vector<int64_t> npix(nplanes);
+  int64_t units = 0;
+  for (int i = 0; i < nplanes; ++i) {
+    const tdct_plane& p = planes[i];
+    char what[64];
+    std::snprintf(what, sizeof what, "%s plane %d", who, i);
+    int rc = check_plane(p.img, p.pitch, p.H, p.W, p.dtype, what);
+    if (rc) return rc;
+    if (p.dtype != TDCT_U8)
+      return fail(TDCT_EUNSUPPORTED, "%s: the sweep takes u8 planes (plane %d is int16)", who, i);
+    if (p.recon) return fail(TDCT_EINVAL, "%s: plane %d: recon must be NULL", who, i);
+    PlaneDesc d = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, 64, nullptr, 0, i);
+    d.chunks = (d.nbx + kSweepUnitBlocks - 1) / kSweepUnitBlocks;
+    d.unit_begin = units;
+    units += (int64_t)d.nby * d.chunks;
+    descs[i] = d;
+    npix[i] = (int64_t)p.H * p.W;
+  }
+  const size_t bytes_desc = sizeof(PlaneDesc) * descs.size();
+  const size_t bytes_npix = sizeof(int64_t) * npix.size();
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, bytes_desc + bytes_npix, s);
+  if (e != cudaSuccess) return fail(TDCT_ENOMEM, "%s: cudaMallocAsync: %s", who, cudaGetErrorString(e));
+  PlaneDesc* d_descs = static_cast<PlaneDesc*>(scratch);
+  int64_t* d_npix = reinterpret_cast<int64_t*>(static_cast<char*>(scratch) + bytes_desc);
+  unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
+  if ((e = cudaMemcpyAsync(d_descs, descs.data(), bytes_desc, cudaMemcpyHostToDevice, s)) ==
+          cudaSuccess &&
+      (e = cudaMemcpyAsync(d_npix, npix.data(), bytes_npix, cudaMemcpyHostToDevice, s)) ==
+          cudaSuccess &&
+      (e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long) * 64 * (size_t)nplanes, s)) ==
+          cudaSuccess) {
+    PlaneTable tab;
+    std::memset(&tab, 0, sizeof tab);
+    tab.d = d_descs;
+    tab.n = nplanes;
+    tab.total_units = units;
+    e = launch_sweep(tab, dct, C, sse, s);
+    if (e == cudaSuccess && d_psnr) {
+      const int n = 64 * nplanes;
+      psnr_sweep_kernel<<<(n + 255) / 256, 256, 0, s>>>(sse, d_npix, d_psnr, n);
+      e = cudaGetLastError();
+    }
+  }
+  const cudaError_t ef = cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  return TDCT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tdct_sweep_batched(const tdct_plane* planes, int nplanes, const int8_t T[64],
+                       const int32_t n[8], uint64_t* d_sse, double* d_psnr,
+                       tdct_stream_t stream) {
+  Transform tr;
+  int rc = resolve_transform(T, n, &tr);
+  if (rc) return rc;
+  if (!tr.t1)
+    return fail(TDCT_EUNSUPPORTED,
+                "tdct_sweep_batched implements T1 (its fast algorithm); use tdct_codec_error_batched "
+                "with one plane per r for another T");
+  const float C[64] = {};
+  return sweep_batched(planes, nplanes, false, C, d_sse, d_psnr,
+                       reinterpret_cast<cudaStream_t>(stream), "tdct_sweep_batched");
+}
+
+int tdct_dct_sweep_batched(const tdct_plane* planes, int nplanes, int precision,
+                           uint64_t* d_sse, double* d_psnr, tdct_stream_t stream) {
+  if (precision != TDCT_FP32)
+    return fail(TDCT_EUNSUPPORTED, "tdct_dct_sweep_batched: precision must be TDCT_FP32");
+  float C[64];
+  for (int k = 0; k < 8; ++k)
+    for (int j = 0; j < 8; ++j) {
+      const double ck = k == 0 ? std::sqrt(1.0 / 8.0) : std::sqrt(2.0 / 8.0);
+      C[8 * k + j] = (float)(ck * std::cos(M_PI * (2.0 * j + 1.0) * k / 16.0));
+    }
+  return sweep_batched(planes, nplanes, true, C, d_sse, d_psnr,
+                       reinterpret_cast<cudaStream_t>(stream), "tdct_dct_sweep_batched");
 }
 
 int tdct_debug_inject_wait_timeout(int enable) {
