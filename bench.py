@@ -528,7 +528,8 @@ def time_ours(args, dist, out):
         rec_big = torch.empty_like(big)
         dsse = torch.zeros(1, dtype=torch.int64, device=dev)
         dct = {}
-        for name, prec in (("fp32", P.TDCT_FP32), ("bf16", P.TDCT_BF16)):
+        for name, prec in (("fp32", P.TDCT_FP32), ("bf16", P.TDCT_BF16),
+                           ("bf16x3", P.TDCT_BF16X3)):
             for _ in range(2):
                 P.tdct_dct_codec_error(big, wl.desc["r"], dsse, precision=prec, recon=rec_big,
                                        stream=stream)
@@ -545,7 +546,9 @@ def time_ours(args, dist, out):
             blocks = big.numel() // 64
             gbs = 2 * big.numel() / (ms / 1e3) / 1e9
             dct[name] = {"ms": ms, "r": wl.desc["r"], "blocks_per_s": blocks / (ms / 1e3),
-                         "hbm_gbs": gbs, "frac_of_measured_hbm": gbs / measured_peaks()[0]}
+                         "hbm_gbs": gbs, "frac_of_measured_hbm": gbs / measured_peaks()[0],
+                         "engine": "CUDA cores (FP32 FMA)" if name == "fp32" else
+                         "tensor cores (tcgen05.mma kind::f16, bf16 operands, FP32 accumulate)"}
         out["dct"] = dct
     plan.close()
     return wl

@@ -64,7 +64,7 @@ enum tdct_status {
 
 enum tdct_dtype { TDCT_U8 = 0, TDCT_I16 = 1 };
 
-enum tdct_precision { TDCT_FP32 = 0, TDCT_BF16 = 1 };
+enum tdct_precision { TDCT_FP32 = 0, TDCT_BF16 = 1, TDCT_BF16X3 = 2 };
 
 /*
  * Forward-transform engines of the fused codec.
@@ -381,9 +381,18 @@ void tdct_plan_destroy(tdct_plan* plan);
 /*
  * tdct_dct_codec_error -- the exact-DCT comparison codec (§6.1 with C the
  * orthonormal 8-point DCT-II of §2, C[k][j] = c_k cos(pi (2j+1) k / 16)).
- *   precision TDCT_FP32: FP32 constants, FP32 arithmetic.
- *             TDCT_BF16: constants and inter-stage values rounded to bf16,
- *             products accumulated in FP32 (the numerics of a bf16 GEMM).
+ *   precision TDCT_FP32: FP32 constants, FP32 arithmetic (CUDA cores).
+ *             TDCT_BF16: bf16 operands, FP32 accumulation.  u8 planes run
+ *             as two GEMMs per 128 blocks on the tensor cores: Y = X (C kron
+ *             C)^T over the kept coefficients (samples exact in bf16, each
+ *             weight C_i[k] C_j[l] rounded once to bf16), then the
+ *             reconstruction from Y rounded to bf16.  int16 planes run on the
+ *             CUDA cores with the separable form (constants, inputs and the
+ *             inter-stage values rounded to bf16, FP32 accumulation).
+ *             Coefficient error stated, not targeted: within 2^-6 of max |Y|.
+ *             TDCT_BF16X3: u8 planes only, the tensor-core GEMMs with three
+ *             bf16 terms per weight and two per coefficient: FP32-level
+ *             accuracy (within 1e-5 of max |Y|, PSNR within 0.01 dB of FP64).
  *   d_coef    output or NULL: float [nby][nbx][8][8], Y = C A C^T
  *   Rounding and clamping as the integer path.  Results are close to, not
  *   identical with, the FP64 definition.

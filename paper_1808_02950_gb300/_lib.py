@@ -15,7 +15,7 @@ from . import build as _build
 TDCT_OK, TDCT_EINVAL, TDCT_ENOTORTHO, TDCT_ECUDA = 0, 1, 2, 3
 TDCT_ETIMEOUT, TDCT_EDEVICE, TDCT_ENOMEM, TDCT_EUNSUPPORTED = 4, 5, 6, 7
 TDCT_U8, TDCT_I16 = 0, 1
-TDCT_FP32, TDCT_BF16 = 0, 1
+TDCT_FP32, TDCT_BF16, TDCT_BF16X3 = 0, 1, 2
 TDCT_PATH_AUTO, TDCT_PATH_BUTTERFLY, TDCT_PATH_TENSOR, TDCT_PATH_TENSOR_PIPELINED = 0, 1, 2, 3
 TDCT_LOAD_PLAIN, TDCT_LOAD_BULK, TDCT_LOAD_STAGED = 0, 1, 2
 

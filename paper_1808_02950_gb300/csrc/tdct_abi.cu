@@ -1426,8 +1426,10 @@ int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dty
   if (rc) return rc;
   if ((rc = check_plane(d_img, pitch, H, W, dtype, "tdct_dct_codec_error"))) return rc;
   if (d_recon && (rc = check_plane(d_recon, recon_pitch, H, W, dtype, "recon"))) return rc;
-  if (precision != TDCT_FP32 && precision != TDCT_BF16)
-    return fail(TDCT_EINVAL, "precision %d is neither TDCT_FP32 nor TDCT_BF16", precision);
+  if (precision != TDCT_FP32 && precision != TDCT_BF16 && precision != TDCT_BF16X3)
+    return fail(TDCT_EINVAL, "precision %d is not a tdct_precision", precision);
+  if (precision == TDCT_BF16X3 && dtype != TDCT_U8)
+    return fail(TDCT_EUNSUPPORTED, "TDCT_BF16X3 takes u8 planes (use TDCT_FP32 for int16)");
   if (!d_sse || (reinterpret_cast<uintptr_t>(d_sse) & 7))
     return fail(TDCT_EINVAL, "d_sse NULL or not 8-byte aligned");
   if (d_coef && (reinterpret_cast<uintptr_t>(d_coef) & 3))
@@ -1437,9 +1439,10 @@ int tdct_dct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dty
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_dct_codec_error memset");
   const PlaneDesc P = make_desc(d_img, pitch, H, W, dtype, r, d_recon, recon_pitch, 0);
-  // bf16 on u8 planes: the two GEMMs on the tensor cores; otherwise the CUDA cores
-  e = (precision == TDCT_BF16 && dtype == TDCT_U8)
-          ? launch_dct_tc(P, d_coef, status_word(), sse, s)
+  // bf16 operands on u8 planes: the two GEMMs on the tensor cores (one bf16
+  // term per weight, or three for FP32-level accuracy); otherwise the CUDA cores
+  e = (precision == TDCT_BF16X3 || (precision == TDCT_BF16 && dtype == TDCT_U8))
+          ? launch_dct_tc(P, precision == TDCT_BF16X3 ? 3 : 1, d_coef, status_word(), sse, s)
           : launch_dct_codec(P, precision, d_coef, sse, s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_dct_codec_error launch");
   if (d_psnr) {

@@ -36,6 +36,7 @@
 #include "tdct_classes.h"
 #include "tdct_kernels.cuh"
 #include "tdct_tc.h"
+#include "tdct_tcgen05.cuh"
 
 namespace tdct {
 
@@ -47,53 +48,6 @@ constexpr int kATileBytes = 16 * 2048;  // 16 K-chunks x 128 rows x 16 bytes
 // Columns per block (a valid N of an M = 128 MMA: a multiple of 16).
 __host__ __device__ constexpr int nh_of(int R) { return R <= 16 ? 16 : (R <= 32 ? 32 : 64); }
 __host__ __device__ constexpr int tmem_cols_of(int N) { return N < 32 ? 32 : N; }
-
-// Instruction descriptor of tcgen05.mma .kind::f16: D FP32 (1 at bit 4),
-// A and B FP16 (0 at bits 7 and 10), both K-major, N >> 3 at bit 17,
-// M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// Shared-memory matrix descriptor, no swizzle (layout type 0), version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                        uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* d) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]),
-                 "=r"(d[6]), "=r"(d[7])
-               : "r"(taddr)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
 
 // fp16 pair (1024 + a, 1024 + b) from bytes of w selected by `sel`.
 __device__ __forceinline__ uint32_t biased_f16x2(uint32_t w, uint32_t sel) {

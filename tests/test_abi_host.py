@@ -131,8 +131,10 @@ def test_forward_and_inverse_reject():
 
 def test_dct_codec_rejects():
     L = P.load()
-    assert L.tdct_dct_codec_error(FAKE, 64, 16, 64, 0, 10, 2, None, None, 0, FAKE, None, None) \
-        == _lib.TDCT_EINVAL
+    assert L.tdct_dct_codec_error(FAKE, 64, 16, 64, 0, 10, 3, None, None, 0, FAKE, None, None) \
+        == _lib.TDCT_EINVAL  # not a tdct_precision
+    assert L.tdct_dct_codec_error(FAKE, 128, 16, 64, 1, 10, _lib.TDCT_BF16X3, None, None, 0, FAKE,
+                                  None, None) == _lib.TDCT_EUNSUPPORTED  # int16 plane
     assert L.tdct_dct_codec_error(FAKE, 64, 16, 64, 0, 99, 0, None, None, 0, FAKE, None, None) \
         == _lib.TDCT_EINVAL
 
