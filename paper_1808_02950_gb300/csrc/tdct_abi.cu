@@ -233,15 +233,22 @@ PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int
   d.chunks = (d.nbx + 63) / 64;
   d.dtype = dtype;
   d.r = r;
-  const bool bulk = dtype == TDCT_U8 && ((reinterpret_cast<uintptr_t>(img) | (uintptr_t)pitch) & 15) == 0 &&
-                    W % 16 == 0 && H % 8 == 0 && (!recon || aligned8(recon, recon_pitch));
+  // bulk-copy ring: 16-byte aligned base, H % 8 == 0, and either 16-byte
+  // aligned rows with W % 16 == 0, or a pitch of 8 mod 16 with W % 16 == 8
+  // (odd rows then start 8 bytes past a boundary; their copies reach 8 bytes
+  // into the previous row, and even rows' last copies 8 bytes into the next)
+  const bool base16 = (reinterpret_cast<uintptr_t>(img) & 15) == 0;
+  const bool shifted = (pitch & 15) == 8 && W % 16 == 8;
+  const bool bulk = dtype == TDCT_U8 && base16 && H % 8 == 0 &&
+                    (((pitch & 15) == 0 && W % 16 == 0) || shifted) &&
+                    (!recon || aligned8(recon, recon_pitch));
   // staged-copy rings: planes that miss the bulk-copy conditions, with 8-byte
   // aligned rows and W % 8 == 0, any height (rows past the bottom edge are
   // zero-filled in shared memory)
   const bool staged = !bulk && aligned8(img, pitch) && W % 8 == 0 &&
                       (!recon || aligned8(recon, recon_pitch));
   d.vec16 = (aligned8(img, pitch) ? 1 : 0) | ((recon && aligned8(recon, recon_pitch)) ? 2 : 0) |
-            (bulk ? 4 : 0) | (staged ? 8 : 0);
+            (bulk ? 4 : 0) | (staged ? 8 : 0) | ((bulk && shifted) ? 16 : 0);
   d.slot = slot;
   return d;
 }
@@ -413,8 +420,9 @@ struct Group {
   int dtype, r;
   int first, count;
   int64_t units;
-  int any_bulk;  // the planes take the bulk-copy ring
-  int staged;    // the planes take the staged-copy ring
+  int any_bulk;     // the planes take the bulk-copy ring
+  int staged;       // the planes take the staged-copy ring
+  int any_shifted;  // bulk planes with rows 8 mod 16 (their own launch; not the tensor engine)
 };
 
 int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& descs,
@@ -433,15 +441,19 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
     if (p.recon && p.recon_pitch < (int64_t)p.W * sample_bytes(p.dtype))
       return fail(TDCT_EINVAL, "plane %d: recon pitch too small", i);
     const PlaneDesc probe = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, p.r, p.recon, p.recon_pitch, i);
-    by_key[{p.dtype, p.r, (probe.vec16 & 4) ? 1 : (probe.vec16 & 8) ? 2 : 0}].push_back(i);
+    // load path: 1 bulk-copy ring (3: its 8 mod 16 rows variant), 2 staged, 0 plain
+    by_key[{p.dtype, p.r,
+            (probe.vec16 & 4) ? ((probe.vec16 & 16) ? 3 : 1) : (probe.vec16 & 8) ? 2 : 0}]
+        .push_back(i);
     npix[i] = (int64_t)p.H * p.W;
   }
   descs.clear();
   groups.clear();
   for (auto& kv : by_key) {
+    const int load = std::get<2>(kv.first);
     Group g{std::get<0>(kv.first), std::get<1>(kv.first), (int)descs.size(),
-            (int)kv.second.size(), 0, std::get<2>(kv.first) == 1 ? 1 : 0,
-            std::get<2>(kv.first) == 2 ? 1 : 0};
+            (int)kv.second.size(), 0, (load == 1 || load == 3) ? 1 : 0, load == 2 ? 1 : 0,
+            load == 3 ? 1 : 0};
     for (int i : kv.second) {
       const tdct_plane& p = planes[i];
       PlaneDesc d = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, p.r, p.recon, p.recon_pitch, i);
@@ -468,11 +480,12 @@ cudaError_t enqueue_batch(const Transform& tr, const std::vector<Group>& groups,
     tab.n = g.count;
     tab.total_units = g.units;
     tab.any_bulk = g.any_bulk;
+    tab.shifted = g.any_shifted;
     tab.staged = g.staged;
     const bool tensor = path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED;
     if (!tr.t1)
       e = dispatch_codec_generic(g.r, g.dtype, tab, tr, sse, s);
-    else if (tensor && g.any_bulk && g.dtype == TDCT_U8)
+    else if (tensor && g.any_bulk && !g.any_shifted && g.dtype == TDCT_U8)
       e = dispatch_codec_tc(g.r, tab, sse, s, ctas_per_sm,
                             path == TDCT_PATH_TENSOR_PIPELINED ? 1 : tc_variant);
     else
@@ -648,6 +661,7 @@ int tdct_codec_error(const void* d_img, int64_t pitch, int H, int W, int dtype,
   tab.one = make_desc(d_img, pitch, H, W, dtype, r, d_recon, recon_pitch, 0);
   tab.total_units = units_of(tab.one);
   tab.any_bulk = (tab.one.vec16 & 4) ? 1 : 0;
+  tab.shifted = (tab.one.vec16 & 16) ? 1 : 0;
   tab.staged = (tab.one.vec16 & 8) ? 1 : 0;
   unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);

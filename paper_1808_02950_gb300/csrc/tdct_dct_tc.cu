@@ -59,7 +59,7 @@ __host__ __device__ constexpr int dt_k2(int N1, int SPLIT) {
 }
 // B1 (SPLIT x N1 x 64) + B2 (64 x K2) elements at the largest N1 = 64.
 __host__ __device__ constexpr int dt_table_elems(int SPLIT) {
-  return SPLIT * 64 * 64 + 64 * dt_k2(64, SPLIT);
+  return SPLIT * 64 * 64 + 64 * dt_k2(64, SPLIT) + 128;  // + 64 float offsets
 }
 
 // The weight tables of every r in the operand layout, built once per device.
@@ -97,6 +97,36 @@ __device__ __forceinline__ uint4 row_to_bf16(uint2 w) {
   return make_uint4(o[0], o[1], o[2], o[3]);
 }
 
+// Bounded wait for phase `parity` of an mbarrier whose waiters sleep: each
+// try_wait suspends the thread for up to `ns` nanoseconds (its hint) instead
+// of returning at once, so 128 threads waiting for a GEMM do not spin on the
+// issue slots that the other CTAs of the SM are using.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint32_t bar, uint32_t parity,
+                                                        long long limit) {
+  if (mbar_try_wait_sleep(bar, parity, 500u)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait_sleep(bar, parity, 500u))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+
+// Eight u8 samples (one block row) -> eight fp16 1024 + x (exact: fp16 has
+// unit spacing on [1024, 2048)), one byte permute per two samples.
+__device__ __forceinline__ uint4 row_to_f16_biased(uint2 w) {
+  return make_uint4(__byte_perm(w.x, 0x64646464u, 0x4140u), __byte_perm(w.x, 0x64646464u, 0x4342u),
+                    __byte_perm(w.y, 0x64646464u, 0x4140u), __byte_perm(w.y, 0x64646464u, 0x4342u));
+}
+
 template <int N1, bool COEF, int SPLIT>
 __global__ void __launch_bounds__(kDtThreads, 4)
     dct_tc_kernel(const PlaneDesc P, const uint16_t* __restrict__ btab, uint64_t kept_mask,
@@ -111,7 +141,8 @@ __global__ void __launch_bounds__(kDtThreads, 4)
   uint8_t* a2 = a1 + A1_BYTES;
   uint8_t* b1 = a2 + A2_BYTES;
   uint8_t* b2 = b1 + B1_BYTES;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(b2 + B2_BYTES);  // [0] GEMM 1, [1] GEMM 2
+  float* off = reinterpret_cast<float*>(b2 + B2_BYTES);  // 64 offsets 1024 sum_p w_np (SPLIT 1)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(off + 64);   // [0] GEMM 1, [1] GEMM 2
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -127,8 +158,8 @@ __global__ void __launch_bounds__(kDtThreads, 4)
     mbar_init(smem_addr(bar + 1), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // weights, once per CTA
-  for (int e = t; e < (B1_BYTES + B2_BYTES) / 16; e += kDtThreads)
+  // weights (and the offsets), once per CTA
+  for (int e = t; e < (B1_BYTES + B2_BYTES + 256) / 16; e += kDtThreads)
     reinterpret_cast<uint4*>(b1)[e] = __ldg(reinterpret_cast<const uint4*>(btab) + e);
   // the bias column of A2 (K index KB = 1.0, the rest of its slice 0)
   {
@@ -179,10 +210,13 @@ __global__ void __launch_bounds__(kDtThreads, 4)
   load_rows(tile * 128 + t, rw);
   for (; tile < tiles; tile += gridDim.x) {
     const int64_t b = tile * 128 + t;
-    // A1 row t: chunk k = row k of the block
+    // A1 row t: chunk k = row k of the block (SPLIT 1: fp16 1024 + x; the
+    // bf16 weights are exact in fp16, and the offset 1024 sum_p w_np of each
+    // coefficient is subtracted after the read-back)
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-      *reinterpret_cast<uint4*>(a1 + k * 2048 + t * 16) = row_to_bf16(rw[k]);
+      *reinterpret_cast<uint4*>(a1 + k * 2048 + t * 16) =
+          SPLIT == 1 ? row_to_f16_biased(rw[k]) : row_to_bf16(rw[k]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
@@ -194,7 +228,8 @@ __global__ void __launch_bounds__(kDtThreads, 4)
         for (int q = 0; q < 4; ++q)
           mma_f16(tmem, smem_desc(a1s + 2 * q * 2048, 2048, 128),
                   smem_desc(b1s + w * (N1 * 128) + 2 * q * (N1 * 16), N1 * 16, 128),
-                  idesc_bf16(128, N1), (w > 0 || q > 0) ? 1u : 0u);
+                  SPLIT == 1 ? idesc_f16(128, N1) : idesc_bf16(128, N1),
+                  (w > 0 || q > 0) ? 1u : 0u);
       mma_commit(bar1);
     }
     // the samples of this block stay in x, the next tile's load is in flight
@@ -202,7 +237,7 @@ __global__ void __launch_bounds__(kDtThreads, 4)
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[k] = rw[k];
     load_rows(b + (int64_t)gridDim.x * 128, rw);
-    bool ok = __syncthreads_and(mbar_wait_bounded(bar1, phase, wait_limit));
+    bool ok = __syncthreads_and(mbar_wait_sleep_bounded(bar1, phase, wait_limit));
     if (!ok) {
       if (t == 0 && status) atomicExch(status, 4 /* TDCT_ETIMEOUT */);
       break;
@@ -214,6 +249,16 @@ __global__ void __launch_bounds__(kDtThreads, 4)
 #pragma unroll
       for (int g = 0; g < N1 / 16; ++g) tmem_ld16(trow + 16 * g, y + 16 * g);
       tmem_wait_ld();
+      if constexpr (SPLIT == 1) {
+#pragma unroll
+        for (int n = 0; n < N1; n += 2) {
+          const float2 o = *reinterpret_cast<const float2*>(off + n);
+          const float2 v = __fadd2_rn(make_float2(__uint_as_float(y[n]), __uint_as_float(y[n + 1])),
+                                      make_float2(-o.x, -o.y));
+          y[n] = __float_as_uint(v.x);
+          y[n + 1] = __float_as_uint(v.y);
+        }
+      }
       if constexpr (COEF) {
         if (b < nb) {
           if ((reinterpret_cast<uintptr_t>(coef) & 15) == 0) {
@@ -278,7 +323,7 @@ __global__ void __launch_bounds__(kDtThreads, 4)
       slice(K2 / 16 - 1, K2 / 16 - 1);  // the bias
       mma_commit(bar2);
     }
-    ok = __syncthreads_and(mbar_wait_bounded(bar2, phase, wait_limit));
+    ok = __syncthreads_and(mbar_wait_sleep_bounded(bar2, phase, wait_limit));
     phase ^= 1u;
     if (!ok) {
       if (t == 0 && status) atomicExch(status, 4 /* TDCT_ETIMEOUT */);
@@ -367,6 +412,19 @@ float bf16_round(double v) {
   return f;
 }
 
+// fp16 bits of a value that fp16 represents exactly (a bf16-rounded weight:
+// 8 significant bits, magnitude in [2^-14, 2^15)); 0 for 0.
+uint16_t f16_bits_exact(double v) {
+  if (v == 0.0) return 0;
+  const uint16_t sign = v < 0 ? 0x8000u : 0u;
+  double a = std::fabs(v);
+  int e = 0;
+  const double m = std::frexp(a, &e);  // a = m 2^e, m in [0.5, 1)
+  const int E = e - 1 + 15;            // biased exponent of 1.f x 2^(e-1)
+  const uint32_t frac = (uint32_t)std::lround((m * 2.0 - 1.0) * 1024.0);
+  return (uint16_t)(sign | ((uint32_t)E << 10) | frac);
+}
+
 uint16_t bf16_bits(double v) {
   const float f = bf16_round(v);
   uint32_t u;
@@ -395,6 +453,7 @@ void build_table(int ti, int SPLIT, uint16_t* out) {
   std::memset(out, 0, sizeof(uint16_t) * dt_table_elems(SPLIT));
   uint16_t* B1 = out;
   uint16_t* B2 = out + SPLIT * N1 * 64;
+  double off64[64] = {};  // SPLIT 1: 1024 sum_p w_np (GEMM 1 takes the samples as 1024 + x)
   for (int n = 0; n < N1; ++n) {
     if (n >= r) continue;
     const int i = pos[n] / 8, j = pos[n] % 8;
@@ -403,7 +462,10 @@ void build_table(int ti, int SPLIT, uint16_t* out) {
         double rest = C[i][k] * C[j][l];
         for (int w = 0; w < SPLIT; ++w) {
           const double term = bf16_round(rest);
-          B1[w * N1 * 64 + kmajor(N1, n, 8 * k + l)] = bf16_bits(term);
+          // SPLIT 1: the bf16 weight re-encoded exactly as fp16 for GEMM 1
+          B1[w * N1 * 64 + kmajor(N1, n, 8 * k + l)] =
+              SPLIT == 1 ? f16_bits_exact(term) : bf16_bits(term);
+          if (SPLIT == 1) off64[n] += 1024.0 * term;
           if (w == 0) B2[kmajor(64, 8 * k + l, n)] = bf16_bits(term);
           if (w == 1 && SPLIT == 3) B2[kmajor(64, 8 * k + l, N1 + n)] = bf16_bits(term);
           rest -= term;
@@ -411,6 +473,9 @@ void build_table(int ti, int SPLIT, uint16_t* out) {
       }
   }
   for (int p = 0; p < 64; ++p) B2[kmajor(64, p, KB)] = 0x3F00u;  // 1/2
+  float off[64];
+  for (int n = 0; n < 64; ++n) off[n] = (float)off64[n];
+  std::memcpy(B2 + 64 * K2, off, sizeof off);
 }
 
 template <int N1, bool COEF, int SPLIT>
@@ -420,7 +485,7 @@ cudaError_t launch_one(const PlaneDesc& P, const uint16_t* tab, uint64_t kept_ma
   // at least 56 KB of shared memory per CTA: then at most 4 CTAs share an SM,
   // whose 512 tensor-memory columns hold exactly 4 allocations of 128
   constexpr size_t kUsed =
-      128 * 64 * 2 + 128 * K2 * 2 + SPLIT * N1 * 64 * 2 + 64 * K2 * 2 + 64;
+      128 * 64 * 2 + 128 * K2 * 2 + SPLIT * N1 * 64 * 2 + 64 * K2 * 2 + 256 + 64;
   constexpr size_t kSmem = kUsed < 56 * 1024 ? 56 * 1024 : kUsed;
   static int sms = 0, per_sm = 0;
   if (sms == 0) {
@@ -429,7 +494,12 @@ cudaError_t launch_one(const PlaneDesc& P, const uint16_t* tab, uint64_t kept_ma
                                                (int)kSmem);
     if (e != cudaSuccess) return e;
     sms = device_sms();
-    per_sm = (int)((227 * 1024) / (kSmem + 1024));
+    int dev = 0, smem_sm = 233472, reserved = 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    }
+    per_sm = (int)(smem_sm / (kSmem + reserved));
     if (per_sm > 4) per_sm = 4;
     if (per_sm < 1) per_sm = 1;
   }

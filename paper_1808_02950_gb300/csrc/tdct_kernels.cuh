@@ -32,7 +32,8 @@ struct PlaneDesc {
   int32_t r;
   int32_t vec16;       // bit 0: img rows 8-byte aligned; bit 1: recon rows;
                        // bit 2: u8 plane eligible for the bulk-copy ring;
-                       // bit 3: plane eligible for a staged-copy ring (u8 or int16)
+                       // bit 3: plane eligible for a staged-copy ring (u8 or int16);
+                       // bit 4: bulk-copy plane whose odd rows start 8 mod 16
   int32_t slot;        // output index for SSE / PSNR
   int32_t pad_;
 };
@@ -44,7 +45,7 @@ struct PlaneTable {
   int64_t total_units;
   PlaneDesc one;
   int32_t staged;      // the planes take a staged-copy ring (vec16 bit 3)
-  int32_t pad_;
+  int32_t shifted;     // bulk-copy planes with rows 8 mod 16 (vec16 bit 4)
 };
 
 __device__ __forceinline__ const PlaneDesc& plane_at(const PlaneTable& t, int i) {
@@ -265,6 +266,13 @@ __device__ __forceinline__ void load_block(const PlaneDesc& P, int by, int bx, b
   }
 }
 
+// min(a, b) then max(., 0) on each signed 16-bit lane.
+__device__ __forceinline__ uint32_t min_relu_s16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.relu.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
 // ---- int16 residual path: one block at a time, epilogue streamed by rows ------
 //
 // Residuals reach |Z| = 36720 (> int16), so the forward is per block in int32.
@@ -272,11 +280,15 @@ __device__ __forceinline__ void load_block(const PlaneDesc& P, int by, int bx, b
 // into rounding, SSE and the store, which keeps no 64-sample output array
 // live.  Rounding half away from zero for both signs:
 //   x' = floor((2N + L^2 - [N < 0]) / (2 L^2)),
-// evaluated as floor((2N + L^2 - [N < 0] + 2048 * 2 L^2) / (2 L^2)) - 2048 so
-// that the dividend stays in [2.2e6, 1.06e9] (|2N| <= 2 * 255 * 8 * L^2 by the
-// orthogonal-projection bound), where mulhi(a, kDivMagic) >> 16 is exact; the
-// offset quotient is clamped to 2048 +- 255.
-constexpr int32_t kI16Bias = (int32_t)(kL2 + 2048u * 2u * kL2);
+// evaluated as q = floor((2N + L^2 - [N < 0] + 255 * 2 L^2) / (2 L^2)) = x' + 255
+// by the multiply-high (exact for dividends in [0, 2.5e9); |2N| <= 2 * 255 *
+// 8 * L^2 by the orthogonal-projection bound, so the dividend is below 6e8,
+// and a negative dividend gives a negative q, which the clamp takes to 0).
+// Two q share a word (high halves of the products, one byte permute), one
+// min.relu.s16x2 clamps both to [0, 510], one vsub2 gives the two int16
+// samples x' = q - 255, and one vabsdiffs2 against the raw sample word gives
+// both |x - x'| for the SSE.
+constexpr int32_t kI16BiasQ = (int32_t)(511u * kL2);
 
 // Where the int16 codec reads a block's row k (8 samples in a uint4): the row
 // words in registers, or a staged-copy slot in shared memory (row stride
@@ -320,31 +332,33 @@ __device__ __forceinline__ uint32_t codec_block_i16(const PlaneDesc& P, int by, 
   }
   const bool store = P.recon != nullptr;
   const bool fast_store = store && full && (P.vec16 & 2);
+  // the valid samples of a row as 16-bit lane masks of its four words
+  uint32_t colmask[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    colmask[m] = (2 * m < valid_cols ? 0xffffu : 0u) | (2 * m + 1 < valid_cols ? 0xffff0000u : 0u);
   uint32_t acc = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    uint32_t n2[8], q[8];
+    uint32_t n2[8];
     inv8<uint32_t>(v + 8 * k, n2);
+    uint32_t h[8];
 #pragma unroll
-    for (int l = 0; l < 8; ++l) {
-      const int32_t a = (int32_t)n2[l] + ((int32_t)n2[l] >> 31) + kI16Bias;
-      q[l] = min(max((uint32_t)__mulhi(a, kDivMagic) >> 16, 2048u - 255u), 2048u + 255u);
-    }
-    uint32_t x[8];
-    unpack_i16x8(rw.row(k), x);
+    for (int l = 0; l < 8; ++l)
+      h[l] = (uint32_t)__mulhi((int32_t)n2[l] + ((int32_t)n2[l] >> 31) + kI16BiasQ, kDivMagic);
+    const uint4 xw = rw.row(k);
+    const uint32_t xs[4] = {xw.x, xw.y, xw.z, xw.w};
+    uint32_t o[4];
     const bool row_in = k < valid_rows;
 #pragma unroll
-    for (int l = 0; l < 8; ++l) {
-      const int32_t d = (int32_t)x[l] + 2048 - (int32_t)q[l];
-      const bool in = full || (row_in && l < valid_cols);
-      acc += in ? (uint32_t)(d * d) : 0u;
+    for (int m = 0; m < 4; ++m) {
+      const uint32_t q = min_relu_s16x2(__byte_perm(h[2 * m], h[2 * m + 1], 0x7632u), 0x01fe01feu);
+      o[m] = __vsub2(q, 0x00ff00ffu);  // x' = q - 255 in each int16 lane
+      uint32_t d = __vabsdiffs2(xs[m], o[m]);
+      if (!full) d &= row_in ? colmask[m] : 0u;
+      acc += (d & 0xffffu) * (d & 0xffffu) + (d >> 16) * (d >> 16);
     }
     if (store && row_in) {
-      // lanes q - 2048 as int16: offset binary (q + 30720, no carry) with the
-      // sign bit flipped
-      uint32_t o[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) o[m] = ((q[2 * m] | (q[2 * m + 1] << 16)) + 0x78007800u) ^ 0x80008000u;
       uint8_t* row = P.recon + (int64_t)(by * 8 + k) * P.recon_pitch + (int64_t)bx * 16;
       if (fast_store) {
         reinterpret_cast<uint2*>(row)[0] = make_uint2(o[0], o[1]);
@@ -400,11 +414,6 @@ __device__ __forceinline__ uint32_t codec_lane_i16(const PlaneDesc& P, int by, i
 // sum x^2 + sum x'^2 - 2 sum x x' from byte dot products (dp4a), exact in
 // uint32 arithmetic since the true value is below 2^32.
 
-__device__ __forceinline__ uint32_t min_relu_s16x2(uint32_t a, uint32_t b) {
-  uint32_t d;
-  asm("min.relu.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-  return d;
-}
 
 // Lanes (block A, block B) of the 8 samples of one row pair: p[l] = a_l +
 // 65536 b_l.  a02 = [a0, 0, a2, 0] supplies both a sample and a zero byte, so
@@ -651,15 +660,18 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8_any(const uint32_t w[64]
 // plane) through the packed forward and the per-block inverse.
 // FULL: the caller guarantees both blocks exist, lie inside the plane and
 // that recon (if any) has 8-byte aligned rows (the bulk-copy planes).
-template <int R, bool FULL = false, typename XS = RowsInRegs>
+// PAIR_OPT (with FULL): the second block may lie past the plane's right
+// edge (planes with an odd number of block columns); it is then skipped.
+template <int R, bool FULL = false, typename XS = RowsInRegs, bool PAIR_OPT = false>
 __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, int bx0, XS xa,
                                                   XS xb, const CodecParams& cp) {
-  const bool has0 = FULL || bx0 < P.nbx, has1 = FULL || bx0 + 1 < P.nbx;
+  const bool has0 = FULL || bx0 < P.nbx;
+  const bool has1 = FULL ? (!PAIR_OPT || bx0 + 1 < P.nbx) : bx0 + 1 < P.nbx;
   if (!has0) return 0u;
   const int valid_rows = FULL ? 8 : min(8, P.H - by * 8);
   const int vc0 = FULL ? 8 : min(8, P.W - bx0 * 8), vc1 = FULL ? 8 : min(8, P.W - (bx0 + 1) * 8);
   const bool full0 = FULL || (valid_rows == 8 && vc0 == 8);
-  const bool full1 = FULL || (has1 && valid_rows == 8 && vc1 == 8);
+  const bool full1 = FULL ? has1 : (has1 && valid_rows == 8 && vc1 == 8);
   uint32_t sse = 0;
 #if !TDCT_SSE_ABSDIFF
 #pragma unroll
@@ -829,6 +841,22 @@ __global__ void __launch_bounds__(256, DT == 0 ? TDCT_U8_MINB : TDCT_I16_MINB) c
 // planes have H % 8 == 0 and W % 16 == 0, so every existing block is full
 // and both blocks of a lane exist together.
 constexpr int kUnitBytes = 8 * 512;
+// Slot rows of the bulk-copy ring: 512 samples plus the 16 bytes a copy of
+// a row that starts 8 bytes past a 16-byte boundary needs (it starts 8 bytes
+// early and rounds its length up to a multiple of 16).
+constexpr int kRingRowBytes = 528;
+constexpr int kRingUnitBytes = 8 * kRingRowBytes;
+
+// A lane's block rows in a bulk-copy ring slot: odd rows of planes whose
+// pitch is 8 mod 16 sit 8 bytes further into their slot row.
+struct RowsInRing {
+  static constexpr bool kInSmem = true;
+  const uint8_t* p;      // row 0 of the block in the slot
+  const uint8_t* p_odd;  // p + the odd rows' shift (0 or 8)
+  __device__ __forceinline__ uint2 row(int k) const {
+    return *reinterpret_cast<const uint2*>((k & 1 ? p_odd : p) + k * kRingRowBytes);
+  }
+};
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -893,15 +921,27 @@ __host__ __device__ constexpr int ring_min_blocks() {
 #endif
 }
 
-template <int R, int STAGES>
+// SHIFT: the launch's planes have a pitch of 8 mod 16 and W % 16 == 8 (odd
+// rows start 8 bytes past a 16-byte boundary; the last pair of a block row
+// has one block): slot rows of 528 bytes, per-row copy offsets and lengths.
+// Otherwise rows are 16-byte aligned with W % 16 == 0: 512-byte slot rows,
+// every pair complete.
+template <bool SHIFT>
+__host__ __device__ constexpr int ring_unit_bytes() {
+  return SHIFT ? kRingUnitBytes : kUnitBytes;
+}
+
+template <int R, int STAGES, bool SHIFT = false>
 __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
     codec_u8_tma_kernel(const PlaneTable tab, const CodecParams cp,
                         unsigned long long* __restrict__ sse_out) {
+  constexpr int UB = ring_unit_bytes<SHIFT>();
+  constexpr int RB = SHIFT ? kRingRowBytes : 512;
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  uint8_t* ring = smem + (size_t)wid * STAGES * kUnitBytes;
-  const uint32_t bars = smem_addr(smem + (size_t)(blockDim.x >> 5) * STAGES * kUnitBytes) +
+  uint8_t* ring = smem + (size_t)wid * STAGES * UB;
+  const uint32_t bars = smem_addr(smem + (size_t)(blockDim.x >> 5) * STAGES * UB) +
                         (uint32_t)(wid * STAGES * 8);
   if (lane == 0) {
 #pragma unroll
@@ -955,15 +995,25 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
     }
     const uint32_t row_bytes = (uint32_t)min(512, pp_W - chunk * 512);
     const uint32_t bar = bars + 8 * s;
+    const uint8_t* src = pp_img + (int64_t)(by * 8 + (lane & 7)) * pp_pitch + (int64_t)chunk * 512;
+    uint32_t off = 0, bytes = row_bytes, total = 8u * row_bytes;
+    if constexpr (SHIFT) {
+      // row `lane` (< 8) of the unit: a row that starts 8 bytes past a
+      // 16-byte boundary (the odd rows) is copied from 8 bytes earlier, and
+      // every copy's length is rounded up to 16 bytes; the host admits such
+      // planes only when those extra bytes lie in the plane's neighbouring
+      // rows (base 16-byte aligned, W % 16 == 8, H % 8 == 0)
+      off = (uint32_t)(reinterpret_cast<uintptr_t>(src) & 15u);
+      bytes = lane < 8 ? ((row_bytes + off + 15u) & ~15u) : 0u;
+      total = __reduce_add_sync(0xffffffffu, bytes);
+    }
     // order this warp's earlier generic reads of the slot before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (lane == 0) mbar_arrive_expect_tx(bar, 8u * row_bytes);
+    if (lane == 0) mbar_arrive_expect_tx(bar, total);
     __syncwarp();
     const bool skip = hook && i == 0;
-    if (lane < 8 && !skip) {
-      const uint8_t* src = pp_img + (int64_t)(by * 8 + lane) * pp_pitch + (int64_t)chunk * 512;
-      bulk_copy_g2s(smem_addr(ring + s * kUnitBytes + lane * 512), src, row_bytes, bar);
-    }
+    if (lane < 8 && !skip)
+      bulk_copy_g2s(smem_addr(ring + s * UB + lane * RB), src - off, bytes, bar);
     issued |= 1u << s;
   };
 
@@ -1016,9 +1066,16 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
     if (!wait_slot(cur_s)) return;
     // the lane's two blocks stay in the slot: the forward reads them, the
     // epilogue reads them again for the SSE; the slot is refilled after
-    const uint8_t* slot = ring + cur_s * kUnitBytes + lane * 16;
-    if (bx0 < P.nbx)
-      acc += codec_pair_u8<R, true>(P, cur_by, bx0, RowsInSmem{slot}, RowsInSmem{slot + 8}, cp);
+    const uint8_t* slot = ring + cur_s * UB + lane * 16;
+    if constexpr (SHIFT) {
+      // odd rows sit 8 bytes into their slot rows; the pair may lack its second block
+      if (bx0 < P.nbx)
+        acc += codec_pair_u8<R, true, RowsInRing, true>(P, cur_by, bx0, RowsInRing{slot, slot + 8},
+                                                        RowsInRing{slot + 8, slot + 16}, cp);
+    } else {
+      if (bx0 < P.nbx)
+        acc += codec_pair_u8<R, true>(P, cur_by, bx0, RowsInSmem{slot}, RowsInSmem{slot + 8}, cp);
+    }
     __syncwarp();
     if (pf < n_units) issue_next();  // refill the slot just used
   }
@@ -1320,8 +1377,9 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
   constexpr int kRingThreads = TDCT_RING_THREADS;
   constexpr int kStages = ring_stages<R>();
   constexpr size_t kSmem = (size_t)(kRingThreads / 32) * kStages * (kUnitBytes + 8);
+  constexpr size_t kSmemShift = (size_t)(kRingThreads / 32) * kStages * (kRingUnitBytes + 8);
   constexpr size_t kSmemStaged = (size_t)(kRingThreads / 32) * kStages * kUnitBytes;
-  static int resident = 0, resident_bulk = 0, resident_staged = 0;  // CTAs per SM, computed once
+  static int resident = 0, resident_bulk = 0, resident_staged = 0, resident_shift = 0;
   static int sms = 0;
   if (resident == 0) {
     sms = device_sms();
@@ -1341,6 +1399,17 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
           &resident_bulk, codec_u8_tma_kernel<R, kStages>, kRingThreads, kSmem);
       if (e != cudaSuccess) return e;
       if (resident_bulk < 1) resident_bulk = 1;
+      e = cudaFuncSetAttribute(codec_u8_tma_kernel<R, kStages, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemShift);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(codec_u8_tma_kernel<R, kStages, true>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &resident_shift, codec_u8_tma_kernel<R, kStages, true>, kRingThreads, kSmemShift);
+      if (e != cudaSuccess) return e;
+      if (resident_shift < 1) resident_shift = 1;
       e = cudaFuncSetAttribute(codec_u8_staged_kernel<R, kStages>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemStaged);
       if (e != cudaSuccess) return e;
@@ -1385,7 +1454,8 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
   }
   const bool bulk = DT == 0 && tab.any_bulk;
   const bool staged = DT == 0 && !bulk && tab.staged;
-  int per_sm = bulk ? resident_bulk : staged ? resident_staged : resident;
+  int per_sm = bulk ? (tab.shifted ? resident_shift : resident_bulk)
+                   : staged ? resident_staged : resident;
   if (cp.ctas_per_sm > 0 && cp.ctas_per_sm < per_sm) per_sm = cp.ctas_per_sm;
   int64_t grid = (int64_t)per_sm * sms;
   const int threads = (bulk || staged) ? kRingThreads : kThreads;
@@ -1395,7 +1465,11 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
   if (grid < 1) grid = 1;
   if constexpr (DT == 0) {
     if (bulk) {
-      codec_u8_tma_kernel<R, kStages><<<(unsigned)grid, kRingThreads, kSmem, s>>>(tab, cp, sse);
+      if (tab.shifted)
+        codec_u8_tma_kernel<R, kStages, true>
+            <<<(unsigned)grid, kRingThreads, kSmemShift, s>>>(tab, cp, sse);
+      else
+        codec_u8_tma_kernel<R, kStages><<<(unsigned)grid, kRingThreads, kSmem, s>>>(tab, cp, sse);
       return cudaGetLastError();
     }
     if (staged) {

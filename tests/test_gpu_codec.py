@@ -238,6 +238,36 @@ def test_bulk_copy_ring_planes(H, W):
         assert sse2 == want_sse
 
 
+@pytest.mark.parametrize("H,W,extra", [(8, 8, 0), (16, 24, 0), (64, 1032, 0), (48, 2056, 16),
+                                       (8, 4104, 0), (40, 520, 32), (64, 1544, 0)])
+def test_bulk_copy_ring_rows_8_mod_16(H, W, extra):
+    """u8 planes with a 16-byte aligned base, W % 16 == 8, pitch 8 mod 16 and
+    H % 8 == 0 take the bulk-copy ring: odd rows start 8 bytes past a 16-byte
+    boundary and are copied from 8 bytes earlier; the last pair of each block
+    row has one block.  Pitched reconstructions too."""
+    rng = np.random.default_rng(H * 13 + W + extra)
+    big = rng.integers(0, 256, (H, W + extra)).astype(np.uint8)
+    img = torch.from_numpy(big).to(DEV)[:, :W]
+    host = big[:, :W]
+    planes_r = P.make_planes([img], [16])
+    plan = P.tdct_plan_create(planes_r, path=P.TDCT_PATH_BUTTERFLY)
+    try:
+        assert plan.groups()[0]["load"] == "bulk"
+    finally:
+        plan.close()
+    for r in (1, 10, 16, 40, 64):
+        sse, rec, _ = run_codec(img, r)
+        want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+        assert np.array_equal(rec, want_rec) and sse == want_sse, r
+        rec_big = torch.full((H, W + 24), 3, dtype=torch.uint8, device=DEV)
+        sse2 = torch.zeros(1, dtype=torch.int64, device=DEV)
+        P.tdct_codec_error(img, r, sse2, recon=rec_big[:, :W])
+        torch.cuda.synchronize()
+        assert int(sse2.item()) == want_sse
+        assert np.array_equal(rec_big[:, :W].cpu().numpy(), want_rec)
+        assert (rec_big[:, W:].cpu().numpy() == 3).all()
+
+
 def test_bulk_copy_ring_many_units_per_warp():
     """Enough units that every warp walks its ring many times, across planes."""
     imgs, _ = synth.batch_1024x1024(DEV, n=48)
@@ -309,15 +339,18 @@ def test_staged_bulk_and_plain_planes_in_one_batch():
 
 
 def test_plan_routes_planes_to_the_intended_load_paths():
-    """Bulk-copy ring for 16-byte aligned u8 rows with W % 16 == 0 and
-    H % 8 == 0; staged-copy ring for other 8-byte aligned rows with W % 8 == 0
-    (u8 and int16, any height); plain loads otherwise."""
+    """Bulk-copy ring for u8 planes with a 16-byte aligned base and H % 8 == 0
+    whose rows are 16-byte aligned with W % 16 == 0, or whose pitch is 8 mod 16
+    with W % 16 == 8; staged-copy ring for other 8-byte aligned rows with
+    W % 8 == 0 (u8 and int16, any height); plain loads otherwise."""
     u8 = lambda H, W: torch.zeros(H, W, dtype=torch.uint8, device=DEV)
     i16 = lambda H, W: torch.zeros(H, W, dtype=torch.int16, device=DEV)
     odd_pitch = torch.zeros(64 * 132, dtype=torch.int16, device=DEV)[2:2 + 64 * 130].view(64, 130)
-    cases = [(u8(64, 1024), "u8", 3, "bulk"), (u8(64, 1032), "u8", 4, "staged"),
+    base8 = torch.zeros(64 * 1032 + 8, dtype=torch.uint8, device=DEV)[8:].view(64, 1032)
+    cases = [(u8(64, 1024), "u8", 3, "bulk"), (u8(64, 1032), "u8", 4, "bulk"),
              (u8(60, 1024), "u8", 5, "staged"), (u8(64, 1030), "u8", 6, "plain"),
-             (i16(540, 960), "i16", 7, "staged"), (odd_pitch[:, :128], "i16", 9, "plain")]
+             (i16(540, 960), "i16", 7, "staged"), (odd_pitch[:, :128], "i16", 9, "plain"),
+             (base8, "u8", 10, "staged"), (u8(64, 1040)[:, :1032], "u8", 11, "staged")]
     planes = P.make_planes([c[0] for c in cases], [c[2] for c in cases])
     plan = P.tdct_plan_create(planes, path=P.TDCT_PATH_BUTTERFLY)
     try:

@@ -41,16 +41,34 @@ def test_u8_epilogue_rounds_half_away_for_nonnegative_N():
 
 
 def test_int16_epilogue_offset_form():
-    # int16: floor((2N + L^2 - [N < 0] + 2048 * 2 L^2) / (2 L^2)) - 2048 equals
-    # round-half-away for both signs; the dividend stays in [0, 1.27e9) for
-    # |N| <= 255 * 8 * L^2 (orthogonal-projection bound), where MAGIC is exact
+    # int16: q = floor((2N + L^2 - [N < 0] + 255 * 2 L^2) / (2 L^2)) by the
+    # multiply-high, clamped to [0, 510] (min.relu.s16x2), minus 255 (vsub2),
+    # equals round-half-away clamped to [-255, 255] for both signs.  For
+    # |N| <= 255 * 8 * L^2 (orthogonal-projection bound) the dividend lies in
+    # [-3569 L^2, 4591 L^2]: below 1.27e9 where MAGIC is exact, and a negative
+    # dividend gives a negative q (clamped to 0).  The upper halves fit int16.
     lim = 255 * 8 * L2
     N = dense_N(lim)
     N = N[np.abs(N) <= lim]
-    a = 2 * N - (N < 0) + L2 + 2048 * D
-    assert a.min() >= 0 and a.max() < 1.27e9
-    q = mulhi_hi16(a, MAGIC) - 2048
-    assert np.array_equal(np.clip(q, -255, 255), np.clip(half_away(N), -255, 255))
+    a = 2 * N - (N < 0) + L2 + 255 * D
+    assert a.max() < 1.27e9
+    q = mulhi_hi16(a, MAGIC)
+    assert np.abs(q).max() < 2 ** 15
+    assert (q[a < 0] < 0).all()
+    x = np.clip(q, 0, 510) - 255
+    assert np.array_equal(x, np.clip(half_away(N), -255, 255))
+
+
+def test_int16_packed_sse_terms():
+    # vabsdiffs2 of an int16 sample pair and its reconstruction gives both
+    # |x - x'| <= 510 in unsigned 16-bit lanes; their squares sum exactly
+    rng = np.random.default_rng(4)
+    x = rng.integers(-255, 256, (2, 100_000))
+    y = rng.integers(-255, 256, (2, 100_000))
+    d = np.abs(x - y)
+    word = (d[0] & 0xFFFF) | ((d[1] & 0xFFFF) << 16)
+    got = (word & 0xFFFF) ** 2 + (word >> 16) ** 2
+    assert np.array_equal(got, ((x - y) ** 2).sum(axis=0))
 
 
 def test_magic_is_exact_on_its_range():
