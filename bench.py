@@ -568,11 +568,26 @@ def oracle_parity(samples, sse_gpu, transform: str = "T1") -> dict:
         i, img, r = item
         return i, int(oc.codec_plane(img, T, r, want_recon=False)[0])
 
-    with ThreadPoolExecutor(max(1, min(os.cpu_count() or 1, len(samples)))) as ex:
+    threads = max(1, min(os.cpu_count() or 1, len(samples)))
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
         got = list(ex.map(one, samples))
+    dt = time.perf_counter() - t0
+    blocks = sum(((img.shape[0] + 7) // 8) * ((img.shape[1] + 7) // 8) for _, img, _ in samples)
+    # one core: the sample planes in order until about a second has passed
+    t1 = time.perf_counter()
+    b1 = 0
+    for _, img, r in samples:
+        oc.codec_plane(img, T, r, want_recon=False)
+        b1 += ((img.shape[0] + 7) // 8) * ((img.shape[1] + 7) // 8)
+        if time.perf_counter() - t1 > 1.0:
+            break
+    d1 = time.perf_counter() - t1
     bad = [i for i, want in got if int(sse_gpu[i]) != want]
     return {"planes": len(got), "mismatches": len(bad), "first_mismatch": bad[0] if bad else None,
-            "check": "per-plane SSE of the timed run vs the C oracle (int64 definition)"}
+            "check": "per-plane SSE of the timed run vs the C oracle (int64 definition)",
+            "oracle_blocks_per_s": blocks / dt, "oracle_cores": threads,
+            "oracle_blocks_per_s_1core": b1 / d1}
 
 
 def time_configs(args, stream) -> dict:

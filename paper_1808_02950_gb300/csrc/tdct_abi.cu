@@ -239,16 +239,21 @@ PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int
   // into the previous row, and even rows' last copies 8 bytes into the next)
   const bool base16 = (reinterpret_cast<uintptr_t>(img) & 15) == 0;
   const bool shifted = (pitch & 15) == 8 && W % 16 == 8;
-  const bool bulk = dtype == TDCT_U8 && base16 && H % 8 == 0 &&
-                    (((pitch & 15) == 0 && W % 16 == 0) || shifted) &&
-                    (!recon || aligned8(recon, recon_pitch));
+  const bool bulk8 = dtype == TDCT_U8 && base16 && H % 8 == 0 &&
+                     (((pitch & 15) == 0 && W % 16 == 0) || shifted) &&
+                     (!recon || aligned8(recon, recon_pitch));
+  // int16: 16-byte aligned base and pitch and W % 8 == 0 (rows of 16-byte
+  // multiples), any H (rows past the bottom edge are zero-filled in the slot)
+  const bool bulk16 = dtype == TDCT_I16 && base16 && (pitch & 15) == 0 && W % 8 == 0 &&
+                      (!recon || aligned8(recon, recon_pitch));
+  const bool bulk = bulk8 || bulk16;
   // staged-copy rings: planes that miss the bulk-copy conditions, with 8-byte
   // aligned rows and W % 8 == 0, any height (rows past the bottom edge are
   // zero-filled in shared memory)
   const bool staged = !bulk && aligned8(img, pitch) && W % 8 == 0 &&
                       (!recon || aligned8(recon, recon_pitch));
   d.vec16 = (aligned8(img, pitch) ? 1 : 0) | ((recon && aligned8(recon, recon_pitch)) ? 2 : 0) |
-            (bulk ? 4 : 0) | (staged ? 8 : 0) | ((bulk && shifted) ? 16 : 0);
+            (bulk ? 4 : 0) | (staged ? 8 : 0) | ((bulk8 && shifted) ? 16 : 0);
   d.slot = slot;
   return d;
 }

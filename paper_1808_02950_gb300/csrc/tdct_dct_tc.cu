@@ -97,29 +97,6 @@ __device__ __forceinline__ uint4 row_to_bf16(uint2 w) {
   return make_uint4(o[0], o[1], o[2], o[3]);
 }
 
-// Bounded wait for phase `parity` of an mbarrier whose waiters sleep: each
-// try_wait suspends the thread for up to `ns` nanoseconds (its hint) instead
-// of returning at once, so 128 threads waiting for a GEMM do not spin on the
-// issue slots that the other CTAs of the SM are using.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(ns)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint32_t bar, uint32_t parity,
-                                                        long long limit) {
-  if (mbar_try_wait_sleep(bar, parity, 500u)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait_sleep(bar, parity, 500u))
-    if (clock64() - t0 > limit) return false;
-  return true;
-}
-
 // Eight u8 samples (one block row) -> eight fp16 1024 + x (exact: fp16 has
 // unit spacing on [1024, 2048)), one byte permute per two samples.
 __device__ __forceinline__ uint4 row_to_f16_biased(uint2 w) {

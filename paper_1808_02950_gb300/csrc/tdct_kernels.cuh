@@ -882,13 +882,27 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
       : "memory");
 }
 
+// Suspend-time hint (ns) of the ring kernels' copy waits: 0 = the hardware's
+// default time limit per try (tuning knob; measured on GB300).
+#ifndef TDCT_RING_WAIT_HINT_NS
+#define TDCT_RING_WAIT_HINT_NS 0
+#endif
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
+#if TDCT_RING_WAIT_HINT_NS > 0
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "n"(TDCT_RING_WAIT_HINT_NS)
+      : "memory");
+#else
   asm volatile(
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
       : "r"(bar), "r"(parity)
       : "memory");
+#endif
   return ok != 0;
 }
 
@@ -1242,6 +1256,11 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
 // the other from the slot.  Two slots per warp (3 CTAs x 4 warps x 16 KB).
 constexpr int kUnitBytesI16 = 8 * 1024;
 constexpr int kStagesI16 = 2;
+// Slots per warp of the int16 bulk-copy ring (3 CTAs x 4 warps x 2 x 8 KB).
+#ifndef TDCT_I16_BULK_STAGES
+#define TDCT_I16_BULK_STAGES 2
+#endif
+constexpr int kStagesI16Bulk = TDCT_I16_BULK_STAGES;
 
 template <int R>
 __global__ void __launch_bounds__(TDCT_RING_THREADS, 3)
@@ -1361,6 +1380,145 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, 3)
   }
 }
 
+// int16 residual planes with a 16-byte aligned base and pitch and W % 8 == 0
+// (any H): the bulk-copy ring with 8 KB units (8 rows x 64 blocks x 16 B).
+// Lanes 0-7 copy one unit row each (cp.async.bulk, the TMA engine, one
+// mbarrier per slot, bounded waits as the u8 ring); rows past the bottom
+// edge are zero-filled in the slot by the consumer (the residual pad).  The
+// lane's two blocks are coded one after the other from the slot, as in the
+// staged-copy kernel; STAGES slots per warp, STAGES - 1 units in flight.
+template <int R, int STAGES>
+__global__ void __launch_bounds__(TDCT_RING_THREADS, 3)
+    codec_i16_tma_kernel(const PlaneTable tab, const CodecParams cp,
+                         unsigned long long* __restrict__ sse_out) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t* ring = smem + (size_t)wid * STAGES * kUnitBytesI16;
+  const uint32_t bars = smem_addr(smem + (size_t)(blockDim.x >> 5) * STAGES * kUnitBytesI16) +
+                        (uint32_t)(wid * STAGES * 8);
+  if (lane == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) mbar_init(bars + 8 * s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t U = tab.total_units;
+  const int64_t u_begin = (U * warp) / nwarps;
+  const int n_units = (int)((U * (warp + 1)) / nwarps - u_begin);
+  const bool hook = cp.test_hook == 1 && warp == 0;
+
+  int64_t pp_pitch = 0;
+  const uint8_t* pp_img = nullptr;
+  int pp_end = -1, pp_W = 0, pp_H = 0, pp_chunks = 1, pp_by = 0, pp_chunk = 0, pp_s = 0;
+  uint32_t issued = 0, phase = 0;
+  int pf = 0;
+  auto issue_next = [&]() {
+    const int i = pf++;
+    const int s = pp_s;
+    pp_s = pp_s + 1 == STAGES ? 0 : pp_s + 1;
+    if (i >= pp_end) {
+      const int64_t u = u_begin + i;
+      const int q = find_plane(tab, u);
+      const PlaneDesc& Q = tab.d ? tab.d[q] : tab.one;
+      pp_img = Q.img;
+      pp_pitch = Q.pitch;
+      pp_W = Q.W;
+      pp_H = Q.H;
+      pp_chunks = Q.chunks;
+      const int64_t e = ((q + 1 < tab.n) ? tab.d[q + 1].unit_begin : U) - u_begin;
+      pp_end = (int)(e < n_units ? e : n_units);
+      const int64_t local = u - Q.unit_begin;
+      pp_by = (int)(local / pp_chunks);
+      pp_chunk = (int)(local - (int64_t)pp_by * pp_chunks);
+    }
+    const int by = pp_by, chunk = pp_chunk;
+    if (++pp_chunk == pp_chunks) {
+      pp_chunk = 0;
+      ++pp_by;
+    }
+    const uint32_t row_bytes = (uint32_t)min(1024, 2 * pp_W - chunk * 1024);  // a multiple of 16
+    const int rows = min(8, pp_H - by * 8);
+    const uint32_t bar = bars + 8 * s;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)rows * row_bytes);
+    __syncwarp();
+    const bool skip = hook && i == 0;
+    if (lane < rows && !skip) {
+      const uint8_t* src = pp_img + (int64_t)(by * 8 + lane) * pp_pitch + (int64_t)chunk * 1024;
+      bulk_copy_g2s(smem_addr(ring + s * kUnitBytesI16 + lane * 1024), src, row_bytes, bar);
+    }
+    issued |= 1u << s;
+  };
+  auto wait_slot = [&](int s) -> bool {
+    const bool ok = __all_sync(0xffffffffu,
+                               mbar_wait_bounded(bars + 8 * s, (phase >> s) & 1u, cp.wait_limit));
+    if (ok) {
+      phase ^= 1u << s;
+      issued &= ~(1u << s);
+      return true;
+    }
+    if (lane == 0 && cp.status) atomicExch(cp.status, 4 /* TDCT_ETIMEOUT */);
+    for (int o = 0; o < STAGES; ++o)
+      if (o != s && (issued >> o & 1u)) mbar_wait_bounded(bars + 8 * o, (phase >> o) & 1u, cp.wait_limit);
+    return false;
+  };
+
+  for (int k = 0; k < STAGES && pf < n_units; ++k) issue_next();
+
+  int p = -1, p_end = -1;
+  PlaneDesc P;
+  int by = 0, chunk = 0, s = 0;
+  unsigned long long acc = 0;
+  for (int i = 0; i < n_units; ++i) {
+    if (i >= p_end) {
+      if (p >= 0) {
+        acc = warp_sum_u64(acc);
+        if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+        acc = 0;
+      }
+      const int64_t u = u_begin + i;
+      p = find_plane(tab, u);
+      P = tab.d ? tab.d[p] : tab.one;
+      const int64_t e = ((p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U) - u_begin;
+      p_end = (int)(e < n_units ? e : n_units);
+      const int64_t local = u - P.unit_begin;
+      by = (int)(local / P.chunks);
+      chunk = (int)(local - (int64_t)by * P.chunks);
+    }
+    const int bx0 = chunk * 64 + 2 * lane;
+    const int cur_by = by, cur_s = s;
+    if (++chunk == P.chunks) {
+      chunk = 0;
+      ++by;
+    }
+    s = s + 1 == STAGES ? 0 : s + 1;
+    if (!wait_slot(cur_s)) return;
+    uint8_t* slot_all = ring + cur_s * kUnitBytesI16;
+    const int valid_rows = min(8, P.H - cur_by * 8);
+    if (valid_rows < 8) {  // the zero pad below the bottom edge (never copied)
+      for (int e = valid_rows * 64 + lane; e < 8 * 64; e += 32)
+        reinterpret_cast<uint4*>(slot_all)[e] = make_uint4(0u, 0u, 0u, 0u);
+      __syncwarp();
+    }
+    const uint8_t* slot = slot_all + lane * 32;
+#pragma unroll 1
+    for (int b = 0; b < 2; ++b) {
+      if (bx0 + b < P.nbx)
+        acc += codec_block_i16<R>(P, cur_by, bx0 + b, I16RowsInSmem{slot + 16 * b}, cp, valid_rows,
+                                  8);
+    }
+    __syncwarp();
+    if (pf < n_units) issue_next();  // refill the slot just used
+  }
+  if (p >= 0) {
+    acc = warp_sum_u64(acc);
+    if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+  }
+}
+
 inline int device_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -1424,6 +1582,35 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
     }
   }
   if constexpr (DT == 1) {
+    if (tab.any_bulk) {
+      constexpr int kSt = kStagesI16Bulk;
+      constexpr size_t kSmemI16B = (size_t)(kRingThreads / 32) * kSt * (kUnitBytesI16 + 8);
+      static int resident_i16b = 0;
+      if (resident_i16b == 0) {
+        cudaError_t e = cudaFuncSetAttribute(codec_i16_tma_kernel<R, kSt>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemI16B);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(codec_i16_tma_kernel<R, kSt>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident_i16b,
+                                                          codec_i16_tma_kernel<R, kSt>,
+                                                          kRingThreads, kSmemI16B);
+        if (e != cudaSuccess) return e;
+        if (resident_i16b < 1) resident_i16b = 1;
+      }
+      int per_sm = resident_i16b;
+      if (cp.ctas_per_sm > 0 && cp.ctas_per_sm < per_sm) per_sm = cp.ctas_per_sm;
+      int64_t grid = (int64_t)per_sm * sms;
+      const int64_t by_work = (tab.total_units + kRingThreads / 32 - 1) / (kRingThreads / 32);
+      if (by_work < grid) grid = by_work;
+      if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+      if (grid < 1) grid = 1;
+      codec_i16_tma_kernel<R, kSt><<<(unsigned)grid, kRingThreads, kSmemI16B, s>>>(tab, cp, sse);
+      return cudaGetLastError();
+    }
     if (tab.staged) {
       constexpr size_t kSmemI16 = (size_t)(kRingThreads / 32) * kStagesI16 * kUnitBytesI16;
       static int resident_i16 = 0;

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, false>())
     // this warp's rows of tile t (in flight since the previous tile)
     bool ok = true;
     if (in_flight) {
-      ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar_raw, raw_phase, cp.wait_limit));
+      ok = __all_sync(0xffffffffu, mbar_wait_sleep_bounded(bar_raw, raw_phase, cp.wait_limit));
       raw_phase ^= 1u;
       in_flight = false;
     }
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, false>())
       mma_commit(bar_mma);
     }
     // CTA-uniform decision: every thread waits (bounded), all agree
-    const bool done = __syncthreads_and(mbar_wait_bounded(bar_mma, phase, cp.wait_limit));
+    const bool done = __syncthreads_and(mbar_wait_sleep_bounded(bar_mma, phase, cp.wait_limit));
     phase ^= 1u;
     if (!done) {
       if (threadIdx.x == 0 && cp.status) atomicExch(cp.status, 4 /* TDCT_ETIMEOUT */);
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, false>())
     }
   }
   // drain a prefetch still in flight (bounded) before the shared memory goes
-  if (in_flight) __all_sync(0xffffffffu, mbar_wait_bounded(bar_raw, raw_phase, cp.wait_limit));
+  if (in_flight) __all_sync(0xffffffffu, mbar_wait_sleep_bounded(bar_raw, raw_phase, cp.wait_limit));
   if (p >= 0) {
     acc = warp_sum_u64(acc);
     if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, true>())
   auto stage_tile = [&]() -> bool {
     bool ok = true;
     if (in_flight) {
-      ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar_raw, raw_phase, cp.wait_limit));
+      ok = __all_sync(0xffffffffu, mbar_wait_sleep_bounded(bar_raw, raw_phase, cp.wait_limit));
       raw_phase ^= 1u;
       in_flight = false;
     }
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, true>())
     // accumulator of tile t
     // warp-uniform: stage_tile below contains warp-collective operations
     bool ok = __all_sync(0xffffffffu,
-                         mbar_wait_bounded(smem_addr(bar + b), (mma_phase >> b) & 1u, cp.wait_limit));
+                         mbar_wait_sleep_bounded(smem_addr(bar + b), (mma_phase >> b) & 1u, cp.wait_limit));
     mma_phase ^= 1u << b;
     mma_pending[b] = false;
     tc_fence_after();
@@ -539,9 +539,9 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<R, true>())
     }
   }
   // drain: copies and MMAs still in flight (bounded) before the memory goes
-  if (in_flight) mbar_wait_bounded(bar_raw, raw_phase, cp.wait_limit);
+  if (in_flight) mbar_wait_sleep_bounded(bar_raw, raw_phase, cp.wait_limit);
   for (int b = 0; b < 2; ++b)
-    if (mma_pending[b]) mbar_wait_bounded(smem_addr(bar + b), (mma_phase >> b) & 1u, cp.wait_limit);
+    if (mma_pending[b]) mbar_wait_sleep_bounded(smem_addr(bar + b), (mma_phase >> b) & 1u, cp.wait_limit);
   if (p >= 0) {
     acc = warp_sum_u64(acc);
     if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);

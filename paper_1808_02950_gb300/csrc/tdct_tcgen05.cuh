@@ -71,4 +71,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* d) {
       : "memory");
 }
 
+// Bounded wait for phase `parity` of an mbarrier whose waiters sleep: each
+// try_wait suspends the thread for up to `ns` nanoseconds (its hint) instead
+// of returning at once, so 128 threads waiting for a GEMM do not spin on the
+// issue slots that the other CTAs of the SM are using.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint32_t bar, uint32_t parity,
+                                                        long long limit) {
+  if (mbar_try_wait_sleep(bar, parity, 500u)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait_sleep(bar, parity, 500u))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+
 }  // namespace tdct

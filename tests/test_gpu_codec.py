@@ -301,14 +301,40 @@ def test_staged_copy_ring_planes(H, W):
         assert sse2 == want_sse
 
 
-@pytest.mark.parametrize("H,W", [(8, 8), (13, 16), (540, 960), (64, 1032), (1080, 1920)])
-def test_int16_staged_copy_ring_planes(H, W):
-    """int16 residual planes with 8-byte aligned rows and W % 8 == 0 take the
-    int16 staged-copy ring; heights that are not multiples of 8 (the 540-row
-    chroma planes) are zero-padded in shared memory."""
+@pytest.mark.parametrize("H,W", [(8, 8), (13, 16), (540, 960), (64, 1032), (1080, 1920),
+                                 (21, 520)])
+def test_int16_bulk_copy_ring_planes(H, W):
+    """int16 residual planes with a 16-byte aligned base and pitch and W % 8 ==
+    0 take the int16 bulk-copy ring; heights that are not multiples of 8 (the
+    540-row chroma planes) are zero-padded in shared memory, widths that are
+    not multiples of 512 give a short last unit."""
     rng = np.random.default_rng(H * 13 + W)
     host = rng.integers(-255, 256, (H, W)).astype(np.int16)
     img = torch.from_numpy(host).to(DEV)
+    for r in ((8, 16) if H * W > 100000 else (1, 8, 16, 40, 64)):
+        sse, rec, _ = run_codec(img, r)
+        want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+        assert np.array_equal(rec, want_rec) and sse == want_sse
+        sse2, _, _ = run_codec(img, r, want_recon=False)
+        assert sse2 == want_sse
+
+
+@pytest.mark.parametrize("H,W", [(8, 16), (13, 24), (540, 968), (64, 1040)])
+def test_int16_staged_copy_ring_planes(H, W):
+    """int16 residual planes whose first sample sits 8 bytes past a 16-byte
+    boundary (rows 8-byte aligned, W % 8 == 0, not bulk-copy eligible) take the
+    int16 staged-copy ring; heights that are not multiples of 8 are
+    zero-padded in shared memory."""
+    rng = np.random.default_rng(H * 17 + W)
+    big = rng.integers(-255, 256, (H, W + 4)).astype(np.int16)
+    img = torch.from_numpy(big).to(DEV)[:, 4:]
+    host = big[:, 4:]
+    planes = P.make_planes([img], [16])
+    plan = P.tdct_plan_create(planes, path=P.TDCT_PATH_BUTTERFLY)
+    try:
+        assert plan.groups()[0]["load"] == "staged"
+    finally:
+        plan.close()
     for r in ((8, 16) if H * W > 100000 else (1, 8, 16, 40, 64)):
         sse, rec, _ = run_codec(img, r)
         want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
@@ -349,7 +375,8 @@ def test_plan_routes_planes_to_the_intended_load_paths():
     base8 = torch.zeros(64 * 1032 + 8, dtype=torch.uint8, device=DEV)[8:].view(64, 1032)
     cases = [(u8(64, 1024), "u8", 3, "bulk"), (u8(64, 1032), "u8", 4, "bulk"),
              (u8(60, 1024), "u8", 5, "staged"), (u8(64, 1030), "u8", 6, "plain"),
-             (i16(540, 960), "i16", 7, "staged"), (odd_pitch[:, :128], "i16", 9, "plain"),
+             (i16(540, 960), "i16", 7, "bulk"), (odd_pitch[:, :128], "i16", 9, "plain"),
+             (torch.zeros(64, 136, dtype=torch.int16, device=DEV)[:, 4:132], "i16", 12, "staged"),
              (base8, "u8", 10, "staged"), (u8(64, 1040)[:, :1032], "u8", 11, "staged")]
     planes = P.make_planes([c[0] for c in cases], [c[2] for c in cases])
     plan = P.tdct_plan_create(planes, path=P.TDCT_PATH_BUTTERFLY)
