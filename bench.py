@@ -72,6 +72,8 @@ def parse():
                     help="skip the angle-search timing (N = 16 and N = 12, P = {-1, 0, 1})")
     ap.add_argument("--no-ssim", action="store_true",
                     help="skip the MSSIM measurement (originals vs reconstructions)")
+    ap.add_argument("--no-generic", action="store_true",
+                    help="skip the generic-T timing (T2, RDCT, T6, T4, LO x 2)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (single_512, sweep_64x512, ragged_2000, "
                          "video_600x1080p)")
@@ -550,6 +552,20 @@ def time_ours(args, dist, out):
                          "engine": "CUDA cores (FP32 FMA)" if name == "fp32" else
                          "tensor cores (tcgen05.mma kind::f16, bf16 operands, FP32 accumulate)"}
         out["dct"] = dct
+    # The generic kernels (NEXT-1: any orthogonal integer T) on the same images,
+    # reconstruction written: every orthogonal matrix of Table 2 besides T1.
+    if not args.no_generic and args.workload == "batch_1024x1024" and args.transform == "T1":
+        gen = {}
+        for name in ("T2", "RDCT", "T6", "T4", "LOx2"):
+            Tg = transforms.NAMED[name]
+            gplan = P.tdct_plan_create(planes, path=P.TDCT_PATH_BUTTERFLY, T=Tg,
+                                       n=transforms.row_norms(Tg))
+            ms = time_launches(lambda: gplan.launch(sse, None, stream), stream, 10)
+            gplan.close()
+            gbs = algo_bytes / (ms / 1e3) / 1e9
+            gen[name] = {"ms": ms, "blocks_per_s": wl.blocks / (ms / 1e3), "hbm_gbs": gbs,
+                         "frac_of_measured_hbm": gbs / measured_peaks()[0]}
+        out["generic"] = gen
     plan.close()
     return wl
 

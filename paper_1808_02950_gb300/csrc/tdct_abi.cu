@@ -138,6 +138,30 @@ int resolve_transform(const int8_t* T, const int32_t* n, Transform* tr) {
   tr->base.magic = (int32_t)magic;
   tr->base.shift = k - 32;
   for (int i = 0; i < 8; ++i) tr->q[i] = (int32_t)(L / n[i]);
+  // even rows symmetric and odd rows antisymmetric: the even/odd kernels
+  bool sym = true;
+  for (int k = 0; k < 8; ++k)
+    for (int l = 0; l < 8; ++l)
+      if (T[8 * k + 7 - l] != ((k & 1) ? -T[8 * k + l] : T[8 * k + l])) sym = false;
+  // two u8 blocks per register in the forward: every |Z_ij| of u8 samples,
+  // 255 * max(sum of positive, sum of negative entries of t_i kron t_j), fits
+  // a signed 16-bit lane, except Z_00 when t_0 >= 0, which may use the
+  // unsigned lane range
+  bool pack = sym, dc_u16 = false;
+  for (int i = 0; i < 8 && pack; ++i)
+    for (int j = 0; j < 8 && pack; ++j) {
+      int64_t pos = 0, neg = 0;
+      for (int k = 0; k < 8; ++k)
+        for (int l = 0; l < 8; ++l) {
+          const int64_t w = (int64_t)T[8 * i + k] * T[8 * j + l];
+          (w > 0 ? pos : neg) += w > 0 ? w : -w;
+        }
+      const int64_t bound = 255 * (pos > neg ? pos : neg);
+      if (bound <= 32767) continue;
+      if (i == 0 && j == 0 && neg == 0 && bound <= 65535) dc_u16 = true;
+      else pack = false;
+    }
+  tr->base.flags = (sym ? kGenSym : 0) | (pack ? kGenPackU8 : 0) | (pack && dc_u16 ? kGenDcU16 : 0);
   return TDCT_OK;
 }
 

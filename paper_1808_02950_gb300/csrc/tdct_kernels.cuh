@@ -1256,11 +1256,20 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
 // the other from the slot.  Two slots per warp (3 CTAs x 4 warps x 16 KB).
 constexpr int kUnitBytesI16 = 8 * 1024;
 constexpr int kStagesI16 = 2;
-// Slots per warp of the int16 bulk-copy ring (3 CTAs x 4 warps x 2 x 8 KB).
-#ifndef TDCT_I16_BULK_STAGES
-#define TDCT_I16_BULK_STAGES 2
+// Slots per warp of the int16 bulk-copy ring.  Measured on GB300 (256
+// planes of 1088 x 1920 residuals): the classes up to 10 are bound by the
+// bytes in flight and run faster with 3 slots (2 CTAs x 4 warps x 3 x 8 KB
+// per SM; class 8: 0.61 -> 0.66 of the measured HBM peak), the larger
+// classes by issue and run faster with 2 slots at 3 CTAs per SM (class 16:
+// 0.64 with 2 slots, 0.60-0.62 with 3).
+template <int R>
+__host__ __device__ constexpr int i16_bulk_stages() {
+#ifdef TDCT_I16_BULK_STAGES
+  return TDCT_I16_BULK_STAGES;
+#else
+  return R <= 10 ? 3 : 2;
 #endif
-constexpr int kStagesI16Bulk = TDCT_I16_BULK_STAGES;
+}
 
 template <int R>
 __global__ void __launch_bounds__(TDCT_RING_THREADS, 3)
@@ -1583,7 +1592,7 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
   }
   if constexpr (DT == 1) {
     if (tab.any_bulk) {
-      constexpr int kSt = kStagesI16Bulk;
+      constexpr int kSt = i16_bulk_stages<R>();
       constexpr size_t kSmemI16B = (size_t)(kRingThreads / 32) * kSt * (kUnitBytesI16 + 8);
       static int resident_i16b = 0;
       if (resident_i16b == 0) {
