@@ -130,11 +130,51 @@ struct RowRaw {
 // stage and both transposes run in 32 bits, elsewhere in 64.
 template <int B, int DT>
 using StageA = std::conditional_t<(B == 16 || DT == 0), uint32_t, long long>;
-// The row inverse (second stage) in 32 bits: 16x16 u8 blocks (see above).
+// The row inverse (second stage) in 32 bits: u8 samples, where the result
+// 2N + L^2 + 128 * 2 L^2 lies within +-(256 B + 257) L^2 < 2^31 for B <= 32
+// (the intermediates may wrap; the ring arithmetic mod 2^32 keeps the result
+// exact).
 template <int B, int DT>
-constexpr bool kStageB32 = (B == 16 && DT == 0);
+constexpr bool kStageB32 = (DT == 0);
 
-template <int B, int DT, int KE>
+// A contiguous run of N tile entries (16-byte aligned) moved with 16-byte
+// accesses: the low 32 bits of each entry in, full entries out.
+template <typename TileT, int N>
+__device__ __forceinline__ void col_load(const TileT* p, uint32_t* v) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+  if constexpr (sizeof(TileT) == 4) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const uint4 t = q[i];
+      v[4 * i] = t.x, v[4 * i + 1] = t.y, v[4 * i + 2] = t.z, v[4 * i + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const uint4 t = q[i];
+      v[2 * i] = t.x, v[2 * i + 1] = t.z;
+    }
+  }
+}
+template <typename TileT, int N, typename V>
+__device__ __forceinline__ void col_store(TileT* p, const V* v) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+  if constexpr (sizeof(TileT) == 4) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i)
+      q[i] = make_uint4((uint32_t)v[4 * i], (uint32_t)v[4 * i + 1], (uint32_t)v[4 * i + 2],
+                        (uint32_t)v[4 * i + 3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const unsigned long long a = (unsigned long long)(long long)v[2 * i];
+      const unsigned long long b = (unsigned long long)(long long)v[2 * i + 1];
+      q[i] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+    }
+  }
+}
+
+template <int B, int DT, int KE, int PF>
 __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const JamParams jp,
                                                         unsigned long long* __restrict__ sse_out) {
   constexpr int BPW = 32 / B;  // blocks per warp
@@ -142,61 +182,102 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   using VA = StageA<B, DT>;
   using VB = std::conditional_t<kStageB32<B, DT>, uint32_t, long long>;
   using TileT = std::conditional_t<std::is_same_v<VA, uint32_t>, int32_t, long long>;
-  __shared__ TileT tile[4][BPW][B][B + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int bsub = lane / B, k = lane % B;
-  const int64_t nbx = (P.W + B - 1) / B, nby = (P.H + B - 1) / B, nb = nbx * nby;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  TileT (*tl)[B + 1] = tile[wid][bsub];
+  // a plane holds fewer than 2^31 blocks (the host checks)
+  const int nbx = (P.W + B - 1) / B, nby = (P.H + B - 1) / B;
+  const int64_t nb = (int64_t)nbx * nby;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   // the column stage: two lanes per column when the kept extent allows (16x16
   // blocks; at 32x32 the extra registers cost a resident CTA and the split
   // measured 2 % slower)
   constexpr bool kSplit = B == 16 && 2 * KE <= B;
+  // The block's KE leading columns, stored column by column (a column is
+  // contiguous, so the column stage moves it with 16-byte accesses): column c
+  // at c * kS, entry of row i at pos(i), where the split stage mirrors the
+  // lower half (rows B - 1 - m at B/2 + m) so that each lane of a column pair
+  // owns one contiguous half.  kS pads a column by 16 bytes; the blocks of a
+  // warp sit 16 banks apart (row accesses of the two halves do not collide).
+  constexpr int kEl = (int)sizeof(TileT);
+  constexpr int kS = B + 16 / kEl;
+  constexpr int kBlkWords = KE * kS * kEl / 4;
+  constexpr int kBlk = (KE * kS + ((16 - kBlkWords % 32 + 32) % 32) * 4 / kEl);
+  __shared__ __align__(16) TileT tile[4][BPW][kBlk];
+  TileT* const tl = tile[wid][bsub];
+  const int pk_ = (kSplit && k >= B / 2) ? (3 * B / 2 - 1 - k) : k;  // pos(k)
   constexpr uint32_t kBlockMask = (2 * KE >= 32) ? 0xffffffffu : ((1u << (2 * KE)) - 1u);
   constexpr uint32_t kSplitMask = B == 16 ? (kBlockMask | (kBlockMask << 16)) : kBlockMask;
   // kept rows of the lane's column in the column stage
   const int hk = kept_height(B, jp.r, kSplit ? (k >> 1) : k);
   // rounding bias folded into the DC input of the row inverse (T's first row
   // is all ones, so it reaches every output): L^2, plus the centring shift
-  // 128 * 2 L^2 where the stage is 64-bit
-  const VB bias = DT == 0 ? (VB)(kStageB32<B, DT> ? jp.L2 : jp.L2 + jp.hiw) : (VB)0;
+  // 128 * 2 L^2 of u8 samples
+  const VB bias = DT == 0 ? (VB)(jp.L2 + jp.hiw) : (VB)0;
+  // the zonal mask and the doubled q_i of the column stage, per lane: entry i
+  // multiplies the i-th output of the lane's column forward (zero where the
+  // position is not kept); held in registers up to 8 entries.  With the
+  // 32-bit row inverse the column's own q_c joins it (the row inverse then
+  // takes V'[k][c] q_c straight from the tile; products wrap mod 2^32, the
+  // result does not).
+  constexpr bool kFoldQ = kStageB32<B, DT>;
+  constexpr int kNQ = kSplit ? KE / 2 : KE;
+  constexpr int kNQR = kNQ <= 8 ? kNQ : 1;
+  int32_t qm2r[kNQR];
+  const int qc = kFoldQ ? jp.q[min(kSplit ? (k >> 1) : k, KE - 1)] : 1;
+  auto qm2_of = [&](int i) {
+    const int ifull = kSplit ? 2 * i + (k & 1) : i;
+    return ifull < hk ? (int32_t)((uint32_t)(2 * jp.q[ifull]) * (uint32_t)qc) : 0;
+  };
+#pragma unroll
+  for (int i = 0; i < kNQR; ++i) qm2r[i] = qm2_of(i);
+  auto qm2 = [&](int i) { return kNQ <= 8 ? qm2r[i < kNQR ? i : 0] : qm2_of(i); };
   unsigned long long acc = 0;
-  // Block geometry of the lane at warp position b (one division; 32-bit when
-  // the plane's block count allows).
+  // Geometry of the lane's block (index base + bsub at warp position base),
+  // stepped by the grid stride without a division per iteration.
   struct Geo {
-    bool valid, full;
     int by, bx;
   };
-  const bool small = nb < ((int64_t)1 << 31);
-  auto geo_of = [&](int64_t b) {
-    Geo g;
-    const int64_t blk = b + bsub;
-    g.valid = blk < nb;
-    if (small) {
-      const int q = (int)blk / (int)nbx;
-      g.by = g.valid ? q : 0;
-      g.bx = g.valid ? (int)blk - q * (int)nbx : 0;
-    } else {
-      g.by = g.valid ? (int)(blk / nbx) : 0;
-      g.bx = g.valid ? (int)(blk - (int64_t)g.by * nbx) : 0;
+  const int nbx_full = P.W / B, nby_full = P.H / B;
+  const int stride = nwarps * BPW;
+  const int sby = stride / nbx, sbx = stride - sby * nbx;
+  auto step = [&](Geo& g) {
+    g.bx += sbx;
+    g.by += sby;
+    if (g.bx >= nbx) {
+      g.bx -= nbx;
+      ++g.by;
     }
-    g.full = g.valid && (g.by + 1) * B <= P.H && (g.bx + 1) * B <= P.W;
-    return g;
   };
-  // The lane's row k of the block at g (zero outside the plane).
-  auto fetch_row = [&](const Geo& g, RowRaw<B, DT>& rr) {
+  Geo gc;  // the block being transformed
+  gc.by = (warp * BPW + bsub) / nbx;
+  gc.bx = (warp * BPW + bsub) - gc.by * nbx;
+  Geo gf = gc;  // the block being fetched
+  // Rows reach the warp through a ring of PF slots in shared memory, filled by
+  // asynchronous 16-byte copies (cp.async, one commit group per iteration):
+  // the loads of the next PF iterations are in flight while one is
+  // transformed.  Each lane reads back only the words it copied (or stored,
+  // for blocks that cross the plane's edge), so the ring needs no barrier.
+  extern __shared__ uint4 jam_ring[];
+  constexpr int kW = RowRaw<B, DT>::kWords;
+  uint4* const ring = jam_ring + ((size_t)wid * PF * 32 + lane) * kW;  // slot s: + s * 32 kW
+  auto fetch_row = [&](const Geo& g, int slot) {
+    uint4* dst = ring + slot * 32 * kW;
     const int fy = g.by * B + k;
-    if (g.full && (jp.aligned & 1)) {
+    if (g.by < nby_full && g.bx < nbx_full && (jp.aligned & 1)) {
       const uint4* src =
           reinterpret_cast<const uint4*>(P.img + (int64_t)fy * P.pitch + (int64_t)g.bx * B * SB);
 #pragma unroll
-      for (int q = 0; q < RowRaw<B, DT>::kWords; ++q) rr.w[q] = __ldg(src + q);
+      for (int q = 0; q < kW; ++q)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(dst + q)),
+                     "l"(src + q)
+                     : "memory");
     } else {
-      uint32_t* u = reinterpret_cast<uint32_t*>(rr.w);
+      uint32_t u[4 * kW];
 #pragma unroll
-      for (int q = 0; q < 4 * RowRaw<B, DT>::kWords; ++q) u[q] = 0u;
-      if (g.valid) {
+      for (int q = 0; q < 4 * kW; ++q) u[q] = 0u;
+      if (g.by < nby) {
 #pragma unroll
         for (int l = 0; l < B; ++l) {
           const uint32_t v = (uint32_t)load_px<DT>(P, fy, g.bx * B + l);
@@ -204,35 +285,61 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
           else u[l >> 1] |= (v & 0xffffu) << (16 * (l & 1));
         }
       }
+#pragma unroll
+      for (int q = 0; q < kW; ++q) dst[q] = make_uint4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
     }
   };
-  // rows are fetched one iteration ahead: the loads of the next blocks are
-  // in flight while the current ones are transformed (measured 8 % faster at
-  // B = 16, 5 % at B = 32)
-  RowRaw<B, DT> raw_next;
-  Geo g_next{};
-  if (warp * BPW < nb) {
-    g_next = geo_of(warp * BPW);
-    fetch_row(g_next, raw_next);
+#pragma unroll
+  for (int s = 0; s < PF; ++s) {
+    if ((int64_t)warp * BPW + (int64_t)s * stride < nb) fetch_row(gf, s);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    step(gf);
   }
-  for (int64_t base = warp * BPW; base < nb; base += nwarps * BPW) {
-    const Geo g = g_next;
-    const RowRaw<B, DT> raw = raw_next;  // the raw row stays for the error
-    if (base + nwarps * BPW < nb) {
-      g_next = geo_of(base + nwarps * BPW);
-      fetch_row(g_next, raw_next);
-    }
-    const bool valid = g.valid, full = g.full;
-    const int by = g.by, bx = g.bx;
+  int slot = 0;
+  for (int64_t base = (int64_t)warp * BPW; base < nb; base += stride) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PF - 1) : "memory");
+    RowRaw<B, DT> raw;  // the raw row stays for the error
+#pragma unroll
+    for (int q = 0; q < kW; ++q) raw.w[q] = ring[slot * 32 * kW + q];
+    if (base + (int64_t)PF * stride < nb) fetch_row(gf, slot);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    step(gf);
+    slot = slot + 1 == PF ? 0 : slot + 1;
+    const int by = gc.by, bx = gc.bx;
+    const bool valid = by < nby, full = by < nby_full && bx < nbx_full;
+    step(gc);
     const int y = by * B + k;
     // rows: t = T x for row k of the block (KE leading outputs)
-    {
+    if constexpr (DT == 0) {
+      // u8: the first JAM stage's sum s_m and difference d_m travel as one
+      // word s_m + 2^16 d_m through the half-size forward, whose outputs are
+      // then a_i + 2^16 b_i (a_i = t_(2i), b_i = t_(2i+1)); exact because
+      // |a_i| <= 12 * 510 * B / 16 and |b_i| <= 12 * 255 * B / 16 fit in 16
+      // bits.  Samples enter uncentred: the rows of T other than the first
+      // sum to zero, so the centring only takes 128 B off t_0.
+      const uint32_t* ru = reinterpret_cast<const uint32_t*>(raw.w);
+      uint32_t pk[B / 2], o[B / 2];
+#pragma unroll
+      for (int m = 0; m < B / 2; ++m) {
+        const int l = B - 1 - m;
+        const uint32_t xx = __byte_perm(ru[m >> 2], 0u, (uint32_t)((m & 3) * 0x101 + 0x4040));
+        const uint32_t yv = __byte_perm(ru[l >> 2], 0u, (uint32_t)((l & 3) + 0x4440));
+        pk[m] = xx + yv * 0xffff0001u;  // x_m (1 + 2^16) + x_l (1 - 2^16)
+      }
+      jam_fwd<B / 2, uint32_t>(pk, o);
+#pragma unroll
+      for (int i = 0; i < KE / 2; ++i) {
+        const int32_t lo = (int32_t)(int16_t)(o[i] & 0xffffu);
+        tl[(2 * i) * kS + pk_] = (TileT)(i == 0 ? lo - 128 * B : lo);
+        tl[(2 * i + 1) * kS + pk_] = (TileT)((int32_t)(o[i] + 0x8000u) >> 16);
+      }
+    } else {
       uint32_t x[B], t[B];
 #pragma unroll
-      for (int l = 0; l < B; ++l) x[l] = (uint32_t)(raw.at(l) - (DT == 0 ? 128 : 0));
+      for (int l = 0; l < B; ++l) x[l] = (uint32_t)raw.at(l);
       jam_fwd<B, uint32_t>(x, t);
 #pragma unroll
-      for (int j = 0; j < KE; ++j) tl[k][j] = (TileT)(int32_t)t[j];
+      for (int j = 0; j < KE; ++j) tl[j * kS + pk_] = (TileT)(int32_t)t[j];
     }
     __syncwarp();
     // columns c < KE: Z[i][c] (i < KE), zonal mask with 2 q_i, inverse along
@@ -244,43 +351,34 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
     if constexpr (kSplit) {
       if (k < 2 * KE) {
         const int c = k >> 1;
-        const uint32_t hm = (k & 1) ? 0xffffffffu : 0u;  // all ones for h = 1
+        const uint32_t sg = (k & 1) ? 0xffffffffu : 1u;  // +1 for h = 0, -1 for h = 1
         uint32_t col[B], v[B / 2], zh[B / 2];
+        col_load<TileT, B>(tl + c * kS, col);  // rows 0..B/2-1, then B-1 down to B/2
 #pragma unroll
-        for (int i = 0; i < B; ++i) col[i] = (uint32_t)tl[i][c];
-#pragma unroll
-        for (int m = 0; m < B / 2; ++m) v[m] = col[m] + (col[B - 1 - m] ^ hm) - hm;
+        for (int m = 0; m < B / 2; ++m) v[m] = col[m] + sg * col[B / 2 + m];
         jam_fwd<B / 2, uint32_t>(v, zh);  // zh[i] = Z[2 i + h][c]
         VA w[B / 2], rh[B / 2];
 #pragma unroll
-        for (int i = 0; i < B / 2; ++i) {
-          const int ifull = 2 * i + (int)(hm & 1u);
-          const int32_t qm = hm ? jp.q[2 * i + 1] : jp.q[2 * i];
-          w[i] = (2 * i < KE && ifull < KE && ifull < hk)
-                     ? (VA)((long long)(int32_t)zh[i] * (2 * qm)) : (VA)0;
-        }
+        for (int i = 0; i < B / 2; ++i) w[i] = i < kNQ ? (VA)(zh[i] * (uint32_t)qm2(i)) : (VA)0;
         jam_inv<B / 2, VA>(w, rh);  // h = 0: u, h = 1: w
-        const int rx = hm ? B - 1 : 0;
+        VA val[B / 2];
 #pragma unroll
         for (int m = 0; m < B / 2; ++m) {
           const VA pm = __shfl_xor_sync(kSplitMask, rh[m], 1);
           // h = 0: row m = u + w; h = 1: row B - 1 - m = u - w
-          const VA val = hm ? pm - rh[m] : rh[m] + pm;
-          tl[m ^ rx][c] = (TileT)val;
+          val[m] = pm + (VA)sg * rh[m];
         }
+        col_store<TileT, B / 2>(tl + c * kS + (k & 1) * (B / 2), val);
       }
     } else if (k < KE) {
       uint32_t col[B], z[B];
-#pragma unroll
-      for (int i = 0; i < B; ++i) col[i] = (uint32_t)tl[i][k];
+      col_load<TileT, B>(tl + k * kS, col);
       jam_fwd<B, uint32_t>(col, z);
       VA w[B], u[B];
 #pragma unroll
-      for (int i = 0; i < B; ++i)
-        w[i] = (i < KE && i < hk) ? (VA)((long long)(int32_t)z[i] * (2 * jp.q[i])) : (VA)0;
+      for (int i = 0; i < B; ++i) w[i] = i < kNQ ? (VA)((long long)(int32_t)z[i] * qm2(i)) : (VA)0;
       jam_inv<B, VA>(w, u);
-#pragma unroll
-      for (int i = 0; i < B; ++i) tl[i][k] = (TileT)u[i];
+      col_store<TileT, B>(tl + k * kS, u);
     }
     __syncwarp();
     // row k: 2N[k][l] + bias = sum_j q_j V'[k][j] T[j][l] (j < KE); round,
@@ -289,7 +387,7 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
       VB v[B], n2[B];
 #pragma unroll
       for (int j = 0; j < B; ++j)
-        v[j] = j < KE ? (VB)tl[k][j] * (VB)jp.q[j] : (VB)0;
+        v[j] = j >= KE ? (VB)0 : kFoldQ ? (VB)tl[j * kS + pk_] : (VB)tl[j * kS + pk_] * (VB)jp.q[j];
       v[0] += bias;
       jam_inv<B, VB>(v, n2);
       RowRaw<B, DT> out;
@@ -299,16 +397,15 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
       uint32_t sse = 0;
       const bool row_in = valid && y < P.H;
       if constexpr (kStageB32<B, DT>) {
-        // n2 = 2N + L^2 exactly; capped at 128 * 2 L^2 and shifted by it (no
-        // wrap), the signed high product with magic16 carries
-        // floor(a / (2 L^2)) = x' in its upper 16 bits (negative below the
-        // window); pairs are clamped to [0, 255] as s16x2 and packed to bytes
+        // n2 = 2N + L^2 + 128 * 2 L^2 exactly (|2N| <= 256 B L^2); the signed
+        // high product with magic16 carries floor(n2 / (2 L^2)) = x' in its
+        // upper 16 bits for 0 <= n2 <= 256 * 2 L^2 (host-checked), at least
+        // 256 above that (the product is monotone) and a negative value below
+        // 0, all within 16 bits (|n2| < 2^31 keeps |x'| < 2^13); pairs are
+        // clamped to [0, 255] as s16x2 and packed to bytes
         uint32_t h[B];
 #pragma unroll
-        for (int l = 0; l < B; ++l) {
-          const int32_t a = min((int32_t)n2[l], jp.hiw) + jp.hiw;
-          h[l] = (uint32_t)__mulhi(a, jp.magic16);
-        }
+        for (int l = 0; l < B; ++l) h[l] = (uint32_t)__mulhi((int32_t)n2[l], jp.magic16);
 #pragma unroll
         for (int q = 0; q < B / 4; ++q) {
           const uint32_t c01 = min_relu_s16x2(__byte_perm(h[4 * q], h[4 * q + 1], 0x7632u), 0x00ff00ffu);
@@ -316,35 +413,6 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
               min_relu_s16x2(__byte_perm(h[4 * q + 2], h[4 * q + 3], 0x7632u), 0x00ff00ffu);
           ou[q] = __byte_perm(c01, c23, 0x6420u);
         }
-        const uint32_t* ru = reinterpret_cast<const uint32_t*>(raw.w);
-        if (full) {
-#pragma unroll
-          for (int q = 0; q < B / 4; ++q) {
-            const uint32_t dq = __vabsdiffu4(ru[q], ou[q]);
-            sse = __dp4a(dq, dq, sse);
-          }
-        } else {
-#pragma unroll
-          for (int l = 0; l < B; ++l) {
-            const bool in = row_in && bx * B + l < P.W;
-            const int32_t d = raw.at(l) - out.at(l);
-            sse += in ? (uint32_t)(d * d) : 0u;
-          }
-        }
-      } else if constexpr (DT == 0) {
-        // 64-bit stage: n2 = 2N + L^2 + 128 * 2 L^2; clamped to [0, limit]
-        // before the 32-bit division (limit itself gives 256 -> 255)
-        uint32_t qv[B];
-#pragma unroll
-        for (int l = 0; l < B; ++l) {
-          const long long a = (long long)n2[l];
-          const uint32_t ac = a < 0 ? 0u : (a > jp.limit ? (uint32_t)jp.limit : (uint32_t)a);
-          qv[l] = min(__umulhi(ac, jp.magic) >> jp.shift, 255u);
-        }
-#pragma unroll
-        for (int q = 0; q < B / 4; ++q)
-          ou[q] = __byte_perm(__byte_perm(qv[4 * q], qv[4 * q + 1], 0x0040u),
-                              __byte_perm(qv[4 * q + 2], qv[4 * q + 3], 0x0040u), 0x5410u);
         const uint32_t* ru = reinterpret_cast<const uint32_t*>(raw.w);
         if (full) {
 #pragma unroll
@@ -394,6 +462,7 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
     }
     __syncwarp();
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0 && acc) atomicAdd(sse_out, acc);
 }
@@ -405,18 +474,40 @@ __host__ __device__ constexpr int jam_extent_class(int ext) {
        : ext <= 16 ? 16 : ext <= 24 ? 24 : 32;
 }
 
+// Ring depth (iterations of row loads in flight per warp).  The kernel is
+// bound by instruction issue, not memory latency: 2 to 4 stages measured
+// within 1 % at B = 16 and 3 % apart at B = 32, where 2 was fastest.
+template <int B, int DT>
+constexpr int jam_stages() {
+#ifdef TDCT_JAM_STAGES
+  return TDCT_JAM_STAGES;
+#else
+  return B == 32 ? 2 : 3;
+#endif
+}
+
 template <int B, int DT, int KE>
 cudaError_t launch_b(const PlaneDesc& P, const JamParams& jp, unsigned long long* sse,
                      cudaStream_t s) {
-  int dev = 0, sms = 148;
-  if (cudaGetDevice(&dev) == cudaSuccess)
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  constexpr int PF = jam_stages<B, DT>();
+  constexpr int kThreads = 128;
+  constexpr size_t kRing = (size_t)(kThreads / 32) * PF * 32 * RowRaw<B, DT>::kWords * 16;
+  auto kern = jam_codec_kernel<B, DT, KE, PF>;
+  static int resident = 0, sms = 0;
+  if (resident == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRing);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, kThreads, kRing);
+    if (e != cudaSuccess) return e;
+    if (resident < 1) resident = 1;
+    sms = device_sms();
+  }
   const int64_t nb = (int64_t)((P.W + B - 1) / B) * ((P.H + B - 1) / B);
   const int64_t warps = (nb + (32 / B) - 1) / (32 / B);
-  int64_t grid = (warps + 3) / 4;
-  if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+  int64_t grid = (warps + kThreads / 32 - 1) / (kThreads / 32);
+  if (grid > (int64_t)resident * sms) grid = (int64_t)resident * sms;
   if (grid < 1) grid = 1;
-  jam_codec_kernel<B, DT, KE><<<(unsigned)grid, 128, 0, s>>>(P, jp, sse);
+  kern<<<(unsigned)grid, kThreads, kRing, s>>>(P, jp, sse);
   return cudaGetLastError();
 }
 
@@ -449,6 +540,9 @@ cudaError_t launch_jam_codec(int B, const PlaneDesc& P, const JamParams& jp,
     for (int j = 0; j < B; ++j)
       if (zz_b(B, i, j) < jp.r) ext = max(ext, max(i, j) + 1);
   const int ke = min(jam_extent_class(ext), B);
+  // the kernel steps block indices in 32-bit integers
+  if (B > 0 && (int64_t)((P.W + B - 1) / B) * ((P.H + B - 1) / B) >= ((int64_t)1 << 30))
+    return cudaErrorInvalidValue;
   if (B == 16)
     return P.dtype == 0 ? launch_ke<16, 0>(ke, P, jp, sse, s) : launch_ke<16, 1>(ke, P, jp, sse, s);
   if (B == 32)

@@ -63,3 +63,28 @@ def test_jam_codec_smooth_image_and_extremes(B, T):
         sse, rec, _ = run(ext, B, T, r)
         want_sse, want_rec = oc.codec_plane_b(ext, T, B, r)
         assert sse == want_sse and np.array_equal(rec, want_rec)
+
+
+@pytest.mark.parametrize("B,T", [(16, M.T16), (32, M.T32)])
+@pytest.mark.parametrize("dtype", [np.uint8, np.int16])
+def test_jam_codec_large_ragged_plane(B, T, dtype):
+    """A plane with more blocks than one grid stride covers (each warp steps
+    through several blocks and the ring wraps), ragged on both edges, as a
+    16-byte aligned plane and as an unaligned pitched view."""
+    rng = np.random.default_rng(B + (dtype == np.int16))
+    H, W = 3000, 3100
+    if dtype == np.uint8:
+        host = rng.integers(0, 256, (H, W + 3)).astype(np.uint8)
+    else:
+        host = rng.integers(-255, 256, (H, W + 3)).astype(np.int16)
+    for off in (0, 3):
+        view = np.ascontiguousarray(host[:, off:off + W]) if off == 0 else host[:, off:off + W]
+        for r in (16, 100):
+            dev = torch.from_numpy(host).to(DEV)[:, off:off + W] if off else torch.from_numpy(view).to(DEV)
+            recon = torch.full((H, W), 7, dtype=dev.dtype, device=DEV)
+            sse = torch.zeros(1, dtype=torch.int64, device=DEV)
+            P.tdct_codec_error_jam(dev, B, T.tolist(), r, sse, recon=recon)
+            torch.cuda.synchronize()
+            want_sse, want_rec = oc.codec_plane_b(np.ascontiguousarray(view), T, B, r)
+            assert int(sse.item()) == want_sse, (off, r)
+            assert np.array_equal(recon.cpu().numpy(), want_rec), (off, r)
