@@ -262,6 +262,8 @@ int tdct_dct_sweep_batched(const tdct_plane* planes, int nplanes, int precision,
  *             kernels implement the JAM fast algorithm)
  *   r         1..B^2
  *   other arguments as tdct_codec_error; edge blocks are zero padded.
+ * Errors: as tdct_codec_error, and TDCT_EINVAL for a plane of 2^30 or more
+ * B x B blocks.
  */
 int tdct_codec_error_jam(const void* d_img, int64_t pitch, int H, int W, int dtype, int B,
                          const int8_t* T, const int32_t* n, int r, void* d_recon,

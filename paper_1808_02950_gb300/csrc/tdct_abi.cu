@@ -1359,6 +1359,9 @@ int tdct_codec_error_jam(const void* d_img, int64_t pitch, int H, int W, int dty
   jp.aligned = (a16(d_img, pitch) ? 1 : 0) | (d_recon && a16(d_recon, recon_pitch) ? 2 : 0);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   unsigned long long* sse = reinterpret_cast<unsigned long long*>(d_sse);
+  const int64_t nblocks = (int64_t)((H + B - 1) / B) * ((W + B - 1) / B);
+  if (nblocks >= ((int64_t)1 << 30))
+    return fail(TDCT_EINVAL, "%lld blocks of %d x %d: at most 2^30 - 1 per plane", (long long)nblocks, B, B);
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e, "tdct_codec_error_jam memset");
   const PlaneDesc P = make_desc(d_img, pitch, H, W, dtype, 64, d_recon, recon_pitch, 0);

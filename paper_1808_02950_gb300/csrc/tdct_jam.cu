@@ -15,19 +15,26 @@
 // 2 q_i and the bias L^2 make the last stage yield 2N + L^2, and
 // x' = floor((2N + L^2) / (2 L^2)) once the value is inside the clamp window
 // (a 32-bit multiply-high with a host-checked constant).  u8 samples enter
-// centred (x - 128; the reconstruction is shifted back by the rounding
-// bias): the kept-coefficient reconstruction is an orthogonal projection,
-// so |x'_exact - 128| <= ||X - 128||_F <= 128 B and |2N| <= 256 B L^2.  For
-// 16x16 u8 blocks that is below 2.13e9 < 2^31 and the second inverse stage
-// runs in 32-bit integers (wrapping intermediates, exact result); for 32x32
-// blocks and int16 residuals it runs in 64-bit integers.
+// as they are: the DC position is always kept and the kept-coefficient
+// reconstruction is an orthogonal projection, so it maps X to
+// 128 + P(X - 128) and |x'_exact - 128| <= ||X - 128||_F <= 128 B; then
+// |2N + L^2 - 256 L^2| <= (256 B + 1) L^2 < 2^31 for B <= 32, and the
+// column and row inverses run in 32-bit integers (wrapping intermediates,
+// exact result).  For int16 residuals the row inverse runs in 64 bits.
 //
 // Work: a lane owns one row of a block (two 16x16 blocks or one 32x32 block
-// per warp); rows are transformed in registers, columns after a transpose
-// through a padded shared-memory tile, and back.  Kernels are compiled per
-// kept-extent class KE (every kept position (i, j) has i, j < KE): the row
-// forward forms KE outputs, only the KE leading columns are transformed, and
-// the row inverse has KE inputs; the exact r is applied at run time.
+// side by side in a warp, NP such groups per iteration); rows are
+// transformed in registers, columns after a transpose through a padded
+// shared-memory tile (column-major, so the column stage moves whole columns
+// with 16-byte accesses), and back.  Rows arrive through a per-warp ring of
+// asynchronous copies.  Kernels are compiled per kept-extent class KE
+// (every kept position (i, j) has i, j < KE): the row forward forms KE
+// outputs, only the KE leading columns are transformed, and the row inverse
+// has KE inputs; the exact r is applied at run time.  The kernel is bound by
+// instruction issue and the integer multiply-add pipe (the multiply-highs of
+// the rounding and most adds land there), so sign flips are written as
+// logic-unit operations and the per-pixel arithmetic is kept to the
+// transforms, one multiply-high, the packing and the byte SSE.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -174,19 +181,21 @@ __device__ __forceinline__ void col_store(TileT* p, const V* v) {
   }
 }
 
-template <int B, int DT, int KE, int PF>
+template <int B, int DT, int KE, int PF, int NP>
 __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const JamParams jp,
                                                         unsigned long long* __restrict__ sse_out) {
-  constexpr int BPW = 32 / B;  // blocks per warp
+  constexpr int BPW = 32 / B;   // blocks side by side in a warp (a lane per row)
+  constexpr int BPI = BPW * NP;  // blocks per warp iteration: NP such groups
   constexpr int SB = DT == 0 ? 1 : 2;
   using VA = StageA<B, DT>;
   using VB = std::conditional_t<kStageB32<B, DT>, uint32_t, long long>;
   using TileT = std::conditional_t<std::is_same_v<VA, uint32_t>, int32_t, long long>;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int bsub = lane / B, k = lane % B;
-  // a plane holds fewer than 2^31 blocks (the host checks)
+  // a plane holds fewer than 2^30 blocks (the host checks), so block
+  // indices, and one grid stride past them, fit in 32 bits
   const int nbx = (P.W + B - 1) / B, nby = (P.H + B - 1) / B;
-  const int64_t nb = (int64_t)nbx * nby;
+  const int nb = nbx * nby;
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   // the column stage: two lanes per column when the kept extent allows (16x16
@@ -203,17 +212,16 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   constexpr int kS = B + 16 / kEl;
   constexpr int kBlkWords = KE * kS * kEl / 4;
   constexpr int kBlk = (KE * kS + ((16 - kBlkWords % 32 + 32) % 32) * 4 / kEl);
-  __shared__ __align__(16) TileT tile[4][BPW][kBlk];
-  TileT* const tl = tile[wid][bsub];
+  __shared__ __align__(16) TileT tile[4][NP][BPW][kBlk];
   const int pk_ = (kSplit && k >= B / 2) ? (3 * B / 2 - 1 - k) : k;  // pos(k)
   constexpr uint32_t kBlockMask = (2 * KE >= 32) ? 0xffffffffu : ((1u << (2 * KE)) - 1u);
   constexpr uint32_t kSplitMask = B == 16 ? (kBlockMask | (kBlockMask << 16)) : kBlockMask;
   // kept rows of the lane's column in the column stage
   const int hk = kept_height(B, jp.r, kSplit ? (k >> 1) : k);
   // rounding bias folded into the DC input of the row inverse (T's first row
-  // is all ones, so it reaches every output): L^2, plus the centring shift
-  // 128 * 2 L^2 of u8 samples
-  const VB bias = DT == 0 ? (VB)(jp.L2 + jp.hiw) : (VB)0;
+  // is all ones, so it reaches every output): L^2 for u8 samples; int16
+  // residuals round half away from zero on |2N| instead
+  const VB bias = DT == 0 ? (VB)jp.L2 : (VB)0;
   // the zonal mask and the doubled q_i of the column stage, per lane: entry i
   // multiplies the i-th output of the lane's column forward (zero where the
   // position is not kept); held in registers up to 8 entries.  With the
@@ -233,13 +241,14 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   for (int i = 0; i < kNQR; ++i) qm2r[i] = qm2_of(i);
   auto qm2 = [&](int i) { return kNQ <= 8 ? qm2r[i < kNQR ? i : 0] : qm2_of(i); };
   unsigned long long acc = 0;
-  // Geometry of the lane's block (index base + bsub at warp position base),
-  // stepped by the grid stride without a division per iteration.
-  struct Geo {
+  // Geometry of the lane's blocks (indices base + p BPW + bsub at warp
+  // position base, p < NP), stepped by the grid stride without a division
+  // per iteration.
+  struct __align__(8) Geo {
     int by, bx;
   };
   const int nbx_full = P.W / B, nby_full = P.H / B;
-  const int stride = nwarps * BPW;
+  const int stride = nwarps * BPI;
   const int sby = stride / nbx, sbx = stride - sby * nbx;
   auto step = [&](Geo& g) {
     g.bx += sbx;
@@ -249,10 +258,13 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
       ++g.by;
     }
   };
-  Geo gc;  // the block being transformed
-  gc.by = (warp * BPW + bsub) / nbx;
-  gc.bx = (warp * BPW + bsub) - gc.by * nbx;
-  Geo gf = gc;  // the block being fetched
+  Geo gf[NP];  // the blocks being fetched
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int blk = warp * BPI + p * BPW + bsub;
+    gf[p].by = blk / nbx;
+    gf[p].bx = blk - gf[p].by * nbx;
+  }
   // Rows reach the warp through a ring of PF slots in shared memory, filled by
   // asynchronous 16-byte copies (cp.async, one commit group per iteration):
   // the loads of the next PF iterations are in flight while one is
@@ -260,9 +272,14 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   // for blocks that cross the plane's edge), so the ring needs no barrier.
   extern __shared__ uint4 jam_ring[];
   constexpr int kW = RowRaw<B, DT>::kWords;
-  uint4* const ring = jam_ring + ((size_t)wid * PF * 32 + lane) * kW;  // slot s: + s * 32 kW
-  auto fetch_row = [&](const Geo& g, int slot) {
-    uint4* dst = ring + slot * 32 * kW;
+  // row p of slot s, per lane: + (s NP + p) 32 kW
+  uint4* const ring = jam_ring + ((size_t)wid * PF * NP * 32 + lane) * kW;
+  // the block geometry of each row, per lane, after the rows
+  Geo* const ring_geo =
+      reinterpret_cast<Geo*>(jam_ring + 4 * PF * NP * 32 * kW) + wid * PF * NP * 32 + lane;
+  auto fetch_row = [&](const Geo& g, int slot, int p) {
+    uint4* dst = ring + (slot * NP + p) * 32 * kW;
+    ring_geo[(slot * NP + p) * 32] = g;
     const int fy = g.by * B + k;
     if (g.by < nby_full && g.bx < nbx_full && (jp.aligned & 1)) {
       const uint4* src =
@@ -291,55 +308,73 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   };
 #pragma unroll
   for (int s = 0; s < PF; ++s) {
-    if ((int64_t)warp * BPW + (int64_t)s * stride < nb) fetch_row(gf, s);
+    if (warp * BPI + s * stride < nb) {
+#pragma unroll
+      for (int p = 0; p < NP; ++p) fetch_row(gf[p], s, p);
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    step(gf);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) step(gf[p]);
   }
   int slot = 0;
-  for (int64_t base = (int64_t)warp * BPW; base < nb; base += stride) {
+  for (int base = warp * BPI; base < nb; base += stride) {
     asm volatile("cp.async.wait_group %0;" ::"n"(PF - 1) : "memory");
-    RowRaw<B, DT> raw;  // the raw row stays for the error
+    RowRaw<B, DT> raws[NP];  // the raw rows stay for the error
+    Geo gc[NP];
 #pragma unroll
-    for (int q = 0; q < kW; ++q) raw.w[q] = ring[slot * 32 * kW + q];
-    if (base + (int64_t)PF * stride < nb) fetch_row(gf, slot);
+    for (int p = 0; p < NP; ++p) {
+#pragma unroll
+      for (int q = 0; q < kW; ++q) raws[p].w[q] = ring[(slot * NP + p) * 32 * kW + q];
+      gc[p] = ring_geo[(slot * NP + p) * 32];
+    }
+    if (base + PF * stride < nb) {
+#pragma unroll
+      for (int p = 0; p < NP; ++p) fetch_row(gf[p], slot, p);
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
-    step(gf);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) step(gf[p]);
     slot = slot + 1 == PF ? 0 : slot + 1;
-    const int by = gc.by, bx = gc.bx;
-    const bool valid = by < nby, full = by < nby_full && bx < nbx_full;
-    step(gc);
-    const int y = by * B + k;
-    // rows: t = T x for row k of the block (KE leading outputs)
-    if constexpr (DT == 0) {
-      // u8: the first JAM stage's sum s_m and difference d_m travel as one
-      // word s_m + 2^16 d_m through the half-size forward, whose outputs are
-      // then a_i + 2^16 b_i (a_i = t_(2i), b_i = t_(2i+1)); exact because
-      // |a_i| <= 12 * 510 * B / 16 and |b_i| <= 12 * 255 * B / 16 fit in 16
-      // bits.  Samples enter uncentred: the rows of T other than the first
-      // sum to zero, so the centring only takes 128 B off t_0.
-      const uint32_t* ru = reinterpret_cast<const uint32_t*>(raw.w);
-      uint32_t pk[B / 2], o[B / 2];
 #pragma unroll
-      for (int m = 0; m < B / 2; ++m) {
-        const int l = B - 1 - m;
-        const uint32_t xx = __byte_perm(ru[m >> 2], 0u, (uint32_t)((m & 3) * 0x101 + 0x4040));
-        const uint32_t yv = __byte_perm(ru[l >> 2], 0u, (uint32_t)((l & 3) + 0x4440));
-        pk[m] = xx + yv * 0xffff0001u;  // x_m (1 + 2^16) + x_l (1 - 2^16)
+    for (int p = 0; p < NP; ++p) {
+      TileT* const tl = tile[wid][p][bsub];
+      const RowRaw<B, DT>& raw = raws[p];
+      // rows: t = T x for row k of the block (KE leading outputs)
+      if constexpr (DT == 0) {
+        // u8: the mirrored samples x_m and x_(B-1-m) travel as one word
+        // x_m + 2^16 x_(B-1-m) through the half-size forward T', whose outputs
+        // are then f_i + 2^16 g_i with f = T' x_(0..B/2-1) and g = T' of the
+        // mirrored half (both within +-12 * 255 * B / 16: exact in 16 bits).
+        // The first JAM stage is linear, so t_(2i) = f_i + g_i and
+        // t_(2i+1) = f_i - g_i.
+        const uint32_t* ru = reinterpret_cast<const uint32_t*>(raw.w);
+        uint32_t pk[B / 2], o[B / 2];
+  #pragma unroll
+        for (int m = 0; m < B / 2; m += 2) {
+          const int l = B - 1 - m;  // l - 1 mirrors m + 1, in the same word as l
+          // bytes x_m, x_(m+1), x_l, x_(l-1)
+          const uint32_t w = __byte_perm(ru[m >> 2], ru[l >> 2],
+                                         (uint32_t)((m & 3) | ((m & 3) + 1) << 4 |
+                                                    (4 + (l & 3)) << 8 | (4 + (l & 3) - 1) << 12));
+          pk[m] = __byte_perm(w, 0u, 0x4240u);
+          pk[m + 1] = __byte_perm(w, 0u, 0x4341u);
+        }
+        jam_fwd<B / 2, uint32_t>(pk, o);
+  #pragma unroll
+        for (int i = 0; i < KE / 2; ++i) {
+          const int32_t f = (int32_t)(int16_t)(o[i] & 0xffffu);
+          const int32_t g = (int32_t)(o[i] + 0x8000u) >> 16;
+          tl[(2 * i) * kS + pk_] = (TileT)(f + g);
+          tl[(2 * i + 1) * kS + pk_] = (TileT)(f - g);
+        }
+      } else {
+        uint32_t x[B], t[B];
+  #pragma unroll
+        for (int l = 0; l < B; ++l) x[l] = (uint32_t)raw.at(l);
+        jam_fwd<B, uint32_t>(x, t);
+  #pragma unroll
+        for (int j = 0; j < KE; ++j) tl[j * kS + pk_] = (TileT)(int32_t)t[j];
       }
-      jam_fwd<B / 2, uint32_t>(pk, o);
-#pragma unroll
-      for (int i = 0; i < KE / 2; ++i) {
-        const int32_t lo = (int32_t)(int16_t)(o[i] & 0xffffu);
-        tl[(2 * i) * kS + pk_] = (TileT)(i == 0 ? lo - 128 * B : lo);
-        tl[(2 * i + 1) * kS + pk_] = (TileT)((int32_t)(o[i] + 0x8000u) >> 16);
-      }
-    } else {
-      uint32_t x[B], t[B];
-#pragma unroll
-      for (int l = 0; l < B; ++l) x[l] = (uint32_t)raw.at(l);
-      jam_fwd<B, uint32_t>(x, t);
-#pragma unroll
-      for (int j = 0; j < KE; ++j) tl[j * kS + pk_] = (TileT)(int32_t)t[j];
     }
     __syncwarp();
     // columns c < KE: Z[i][c] (i < KE), zonal mask with 2 q_i, inverse along
@@ -348,113 +383,128 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
     // of the first JAM stage, the half-size forward and inverse, and the
     // pair combines u +- w by one exchange; otherwise one lane per column.
     // Lanes write only the column they read.
-    if constexpr (kSplit) {
-      if (k < 2 * KE) {
-        const int c = k >> 1;
-        const uint32_t sg = (k & 1) ? 0xffffffffu : 1u;  // +1 for h = 0, -1 for h = 1
-        uint32_t col[B], v[B / 2], zh[B / 2];
-        col_load<TileT, B>(tl + c * kS, col);  // rows 0..B/2-1, then B-1 down to B/2
 #pragma unroll
-        for (int m = 0; m < B / 2; ++m) v[m] = col[m] + sg * col[B / 2 + m];
-        jam_fwd<B / 2, uint32_t>(v, zh);  // zh[i] = Z[2 i + h][c]
-        VA w[B / 2], rh[B / 2];
-#pragma unroll
-        for (int i = 0; i < B / 2; ++i) w[i] = i < kNQ ? (VA)(zh[i] * (uint32_t)qm2(i)) : (VA)0;
-        jam_inv<B / 2, VA>(w, rh);  // h = 0: u, h = 1: w
-        VA val[B / 2];
-#pragma unroll
-        for (int m = 0; m < B / 2; ++m) {
-          const VA pm = __shfl_xor_sync(kSplitMask, rh[m], 1);
-          // h = 0: row m = u + w; h = 1: row B - 1 - m = u - w
-          val[m] = pm + (VA)sg * rh[m];
+    for (int p = 0; p < NP; ++p) {
+      TileT* const tl = tile[wid][p][bsub];
+      if constexpr (kSplit) {
+        if (k < 2 * KE) {
+          const int c = k >> 1;
+          // sign flips as (x ^ hm) - hm (hm all ones for h = 1): logic-unit
+          // operations, which leave the multiply-add pipe (the busier one here)
+          // to the transforms
+          const uint32_t hm = (k & 1) ? 0xffffffffu : 0u;
+          uint32_t col[B], v[B / 2], zh[B / 2];
+          col_load<TileT, B>(tl + c * kS, col);  // rows 0..B/2-1, then B-1 down to B/2
+  #pragma unroll
+          for (int m = 0; m < B / 2; ++m) v[m] = col[m] + (col[B / 2 + m] ^ hm) - hm;
+          jam_fwd<B / 2, uint32_t>(v, zh);  // zh[i] = Z[2 i + h][c]
+          VA w[B / 2], rh[B / 2];
+  #pragma unroll
+          for (int i = 0; i < B / 2; ++i) w[i] = i < kNQ ? (VA)(zh[i] * (uint32_t)qm2(i)) : (VA)0;
+          jam_inv<B / 2, VA>(w, rh);  // h = 0: u, h = 1: w
+          VA val[B / 2];
+  #pragma unroll
+          for (int m = 0; m < B / 2; ++m) {
+            const VA pm = __shfl_xor_sync(kSplitMask, rh[m], 1);
+            // h = 0: row m = u + w; h = 1: row B - 1 - m = u - w
+            val[m] = pm + (rh[m] ^ hm) - hm;
+          }
+          col_store<TileT, B / 2>(tl + c * kS + (k & 1) * (B / 2), val);
         }
-        col_store<TileT, B / 2>(tl + c * kS + (k & 1) * (B / 2), val);
+      } else if (k < KE) {
+        uint32_t col[B], z[B];
+        col_load<TileT, B>(tl + k * kS, col);
+        jam_fwd<B, uint32_t>(col, z);
+        VA w[B], u[B];
+  #pragma unroll
+        for (int i = 0; i < B; ++i) w[i] = i < kNQ ? (VA)((long long)(int32_t)z[i] * qm2(i)) : (VA)0;
+        jam_inv<B, VA>(w, u);
+        col_store<TileT, B>(tl + k * kS, u);
       }
-    } else if (k < KE) {
-      uint32_t col[B], z[B];
-      col_load<TileT, B>(tl + k * kS, col);
-      jam_fwd<B, uint32_t>(col, z);
-      VA w[B], u[B];
-#pragma unroll
-      for (int i = 0; i < B; ++i) w[i] = i < kNQ ? (VA)((long long)(int32_t)z[i] * qm2(i)) : (VA)0;
-      jam_inv<B, VA>(w, u);
-      col_store<TileT, B>(tl + k * kS, u);
     }
     __syncwarp();
-    // row k: 2N[k][l] + bias = sum_j q_j V'[k][j] T[j][l] (j < KE); round,
-    // clamp, error, store
-    {
-      VB v[B], n2[B];
 #pragma unroll
-      for (int j = 0; j < B; ++j)
-        v[j] = j >= KE ? (VB)0 : kFoldQ ? (VB)tl[j * kS + pk_] : (VB)tl[j * kS + pk_] * (VB)jp.q[j];
-      v[0] += bias;
-      jam_inv<B, VB>(v, n2);
-      RowRaw<B, DT> out;
-      uint32_t* ou = reinterpret_cast<uint32_t*>(out.w);
-#pragma unroll
-      for (int q = 0; q < 4 * RowRaw<B, DT>::kWords; ++q) ou[q] = 0u;
-      uint32_t sse = 0;
-      const bool row_in = valid && y < P.H;
-      if constexpr (kStageB32<B, DT>) {
-        // n2 = 2N + L^2 + 128 * 2 L^2 exactly (|2N| <= 256 B L^2); the signed
-        // high product with magic16 carries floor(n2 / (2 L^2)) = x' in its
-        // upper 16 bits for 0 <= n2 <= 256 * 2 L^2 (host-checked), at least
-        // 256 above that (the product is monotone) and a negative value below
-        // 0, all within 16 bits (|n2| < 2^31 keeps |x'| < 2^13); pairs are
-        // clamped to [0, 255] as s16x2 and packed to bytes
-        uint32_t h[B];
-#pragma unroll
-        for (int l = 0; l < B; ++l) h[l] = (uint32_t)__mulhi((int32_t)n2[l], jp.magic16);
-#pragma unroll
-        for (int q = 0; q < B / 4; ++q) {
-          const uint32_t c01 = min_relu_s16x2(__byte_perm(h[4 * q], h[4 * q + 1], 0x7632u), 0x00ff00ffu);
-          const uint32_t c23 =
-              min_relu_s16x2(__byte_perm(h[4 * q + 2], h[4 * q + 3], 0x7632u), 0x00ff00ffu);
-          ou[q] = __byte_perm(c01, c23, 0x6420u);
-        }
-        const uint32_t* ru = reinterpret_cast<const uint32_t*>(raw.w);
-        if (full) {
-#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      TileT* const tl = tile[wid][p][bsub];
+      const RowRaw<B, DT>& raw = raws[p];
+      const int by = gc[p].by, bx = gc[p].bx;
+      const bool valid = by < nby, full = by < nby_full && bx < nbx_full;
+      const int y = by * B + k;
+      // row k: 2N[k][l] + bias = sum_j q_j V'[k][j] T[j][l] (j < KE); round,
+      // clamp, error, store
+      {
+        VB v[B], n2[B];
+  #pragma unroll
+        for (int j = 0; j < B; ++j)
+          v[j] = j >= KE ? (VB)0 : kFoldQ ? (VB)tl[j * kS + pk_] : (VB)tl[j * kS + pk_] * (VB)jp.q[j];
+        v[0] += bias;
+        jam_inv<B, VB>(v, n2);
+        RowRaw<B, DT> out;
+        uint32_t* ou = reinterpret_cast<uint32_t*>(out.w);
+  #pragma unroll
+        for (int q = 0; q < 4 * RowRaw<B, DT>::kWords; ++q) ou[q] = 0u;
+        uint32_t sse = 0;
+        const bool row_in = valid && y < P.H;
+        if constexpr (kStageB32<B, DT>) {
+          // n2 = 2N + L^2 exactly (|n2 - 256 L^2| <= (256 B + 1) L^2); the signed
+          // high product with magic16 carries floor(n2 / (2 L^2)) = x' in its
+          // upper 16 bits for 0 <= n2 <= 256 * 2 L^2 (host-checked), at least
+          // 256 above that (the product is monotone) and a negative value below
+          // 0, all within 16 bits (|n2| < 2^31 keeps |x'| < 2^13); pairs are
+          // clamped to [0, 255] as s16x2 and packed to bytes
+          uint32_t h[B];
+  #pragma unroll
+          for (int l = 0; l < B; ++l) h[l] = (uint32_t)__mulhi((int32_t)n2[l], jp.magic16);
+  #pragma unroll
           for (int q = 0; q < B / 4; ++q) {
-            const uint32_t dq = __vabsdiffu4(ru[q], ou[q]);
-            sse = __dp4a(dq, dq, sse);
+            const uint32_t c01 = min_relu_s16x2(__byte_perm(h[4 * q], h[4 * q + 1], 0x7632u), 0x00ff00ffu);
+            const uint32_t c23 =
+                min_relu_s16x2(__byte_perm(h[4 * q + 2], h[4 * q + 3], 0x7632u), 0x00ff00ffu);
+            ou[q] = __byte_perm(c01, c23, 0x6420u);
+          }
+          const uint32_t* ru = reinterpret_cast<const uint32_t*>(raw.w);
+          if (full) {
+  #pragma unroll
+            for (int q = 0; q < B / 4; ++q) {
+              const uint32_t dq = __vabsdiffu4(ru[q], ou[q]);
+              sse = __dp4a(dq, dq, sse);
+            }
+          } else {
+  #pragma unroll
+            for (int l = 0; l < B; ++l) {
+              const bool in = row_in && bx * B + l < P.W;
+              const int32_t d = raw.at(l) - out.at(l);
+              sse += in ? (uint32_t)(d * d) : 0u;
+            }
           }
         } else {
-#pragma unroll
+          // int16 residuals: |x'| rounded half away from zero, clamped to 255
+  #pragma unroll
           for (int l = 0; l < B; ++l) {
-            const bool in = row_in && bx * B + l < P.W;
-            const int32_t d = raw.at(l) - out.at(l);
+            const long long nn = (long long)n2[l];
+            const long long a = (nn < 0 ? -nn : nn) + jp.L2;
+            int32_t m = a >= jp.limit ? 255 : (int32_t)(__umulhi((uint32_t)a, jp.magic) >> jp.shift);
+            m = min(m, 255);
+            const int32_t xr = nn < 0 ? -m : m;
+            ou[l >> 1] |= ((uint32_t)xr & 0xffffu) << (16 * (l & 1));
+            const bool in = full || (row_in && bx * B + l < P.W);
+            const int32_t d = raw.at(l) - xr;
             sse += in ? (uint32_t)(d * d) : 0u;
           }
         }
-      } else {
-        // int16 residuals: |x'| rounded half away from zero, clamped to 255
-#pragma unroll
-        for (int l = 0; l < B; ++l) {
-          const long long nn = (long long)n2[l];
-          const long long a = (nn < 0 ? -nn : nn) + jp.L2;
-          int32_t m = a >= jp.limit ? 255 : (int32_t)(__umulhi((uint32_t)a, jp.magic) >> jp.shift);
-          m = min(m, 255);
-          const int32_t xr = nn < 0 ? -m : m;
-          ou[l >> 1] |= ((uint32_t)xr & 0xffffu) << (16 * (l & 1));
-          const bool in = full || (row_in && bx * B + l < P.W);
-          const int32_t d = raw.at(l) - xr;
-          sse += in ? (uint32_t)(d * d) : 0u;
-        }
-      }
-      acc += sse;
-      if (P.recon && row_in) {
-        uint8_t* rrow = P.recon + (int64_t)y * P.recon_pitch + (int64_t)bx * B * SB;
-        if (full && (jp.aligned & 2)) {
-#pragma unroll
-          for (int q = 0; q < RowRaw<B, DT>::kWords; ++q) reinterpret_cast<uint4*>(rrow)[q] = out.w[q];
-        } else {
-#pragma unroll
-          for (int l = 0; l < B; ++l) {
-            if (bx * B + l < P.W) {
-              if constexpr (DT == 0) rrow[l] = (uint8_t)out.at(l);
-              else reinterpret_cast<int16_t*>(rrow)[l] = (int16_t)out.at(l);
+        acc += sse;
+        if (P.recon && row_in) {
+          uint8_t* rrow = P.recon + (int64_t)y * P.recon_pitch + (int64_t)bx * B * SB;
+          if (full && (jp.aligned & 2)) {
+  #pragma unroll
+            for (int q = 0; q < RowRaw<B, DT>::kWords; ++q) reinterpret_cast<uint4*>(rrow)[q] = out.w[q];
+          } else {
+  #pragma unroll
+            for (int l = 0; l < B; ++l) {
+              if (bx * B + l < P.W) {
+                if constexpr (DT == 0) rrow[l] = (uint8_t)out.at(l);
+                else reinterpret_cast<int16_t*>(rrow)[l] = (int16_t)out.at(l);
+              }
             }
           }
         }
@@ -475,14 +525,27 @@ __host__ __device__ constexpr int jam_extent_class(int ext) {
 }
 
 // Ring depth (iterations of row loads in flight per warp).  The kernel is
-// bound by instruction issue, not memory latency: 2 to 4 stages measured
-// within 1 % at B = 16 and 3 % apart at B = 32, where 2 was fastest.
+// bound by instruction issue and the integer multiply-add pipe, not memory
+// latency: 2 stages were fastest at both block sizes, 4 up to 4 % slower.
 template <int B, int DT>
 constexpr int jam_stages() {
 #ifdef TDCT_JAM_STAGES
   return TDCT_JAM_STAGES;
 #else
-  return B == 32 ? 2 : 3;
+  return 2;
+#endif
+}
+
+// Block groups per warp iteration: at 16x16 u8 blocks two amortise the
+// ring, geometry and loop work of an iteration over twice the blocks (2 %
+// faster); at 32x32 the registers of a second group cost resident warps (4 %
+// slower), and int16 residuals (64-bit row inverse) keep one as well.
+template <int B, int DT>
+constexpr int jam_groups() {
+#ifdef TDCT_JAM_GROUPS
+  return TDCT_JAM_GROUPS;
+#else
+  return (B == 16 && DT == 0) ? 2 : 1;
 #endif
 }
 
@@ -490,9 +553,11 @@ template <int B, int DT, int KE>
 cudaError_t launch_b(const PlaneDesc& P, const JamParams& jp, unsigned long long* sse,
                      cudaStream_t s) {
   constexpr int PF = jam_stages<B, DT>();
+  constexpr int NP = jam_groups<B, DT>();
   constexpr int kThreads = 128;
-  constexpr size_t kRing = (size_t)(kThreads / 32) * PF * 32 * RowRaw<B, DT>::kWords * 16;
-  auto kern = jam_codec_kernel<B, DT, KE, PF>;
+  constexpr size_t kRing =
+      (size_t)(kThreads / 32) * PF * NP * 32 * (RowRaw<B, DT>::kWords * 16 + 8);
+  auto kern = jam_codec_kernel<B, DT, KE, PF, NP>;
   static int resident = 0, sms = 0;
   if (resident == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRing);
@@ -503,7 +568,7 @@ cudaError_t launch_b(const PlaneDesc& P, const JamParams& jp, unsigned long long
     sms = device_sms();
   }
   const int64_t nb = (int64_t)((P.W + B - 1) / B) * ((P.H + B - 1) / B);
-  const int64_t warps = (nb + (32 / B) - 1) / (32 / B);
+  const int64_t warps = (nb + (32 / B) * NP - 1) / ((32 / B) * NP);
   int64_t grid = (warps + kThreads / 32 - 1) / (kThreads / 32);
   if (grid > (int64_t)resident * sms) grid = (int64_t)resident * sms;
   if (grid < 1) grid = 1;
