@@ -7,11 +7,14 @@
 // Per block: Y = C X C^T (rows, then columns), zonal mask of the first r
 // zig-zag coefficients, X' = C^T Y' C, round half away from zero, clamp, SSE.
 //   FP32: FP32 arithmetic.  The 8-point transforms use the even/odd split of
-//         the DCT (C[k][7-l] = (-1)^k C[k][l]): 8 additions, then 4-term
-//         products on the sums (even k) or differences (odd k), and the
-//         mirror image for the inverse.  Kernels are compiled per r-class:
+//         the DCT (C[k][7-l] = (-1)^k C[k][l]): 8 additions, then products on
+//         the sums (even k, factorised further) or differences (odd k), and
+//         the mirror image for the inverse.  Kernels are compiled per r-class:
 //         coefficients outside the class are never formed (as in the integer
-//         path), the exact r is applied by a mask.
+//         path), the exact r is applied by a mask.  u8 planes without the
+//         coefficient output run two blocks per lane as FP32 pairs
+//         (dct_fp32_pair_kernel); int16 planes and the coefficient output one
+//         block per lane.
 //   BF16: constants, inputs and every inter-stage value rounded to bf16,
 //         products accumulated in FP32 -- the numerics of chaining bf16 GEMMs
 //         with FP32 accumulation -- as direct 8-term products in the order of
