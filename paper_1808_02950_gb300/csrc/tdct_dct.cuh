@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128) dct_codec_kernel(const PlaneDesc P, const
 // reads back only what it copied or stored, so the ring needs no barrier;
 // the rows are read twice (forward, SSE) and the slot refilled after.
 // Work: units of one block row x 64 blocks (32 pairs), contiguous ranges of
-// units per warp.
+// units per warp; ring depth 3 (2 and 4 measured the same).
 struct DctK {
   float2 c0, c4, c1, c2, c3, c5, c6, c7;
 };
@@ -401,9 +401,16 @@ __device__ __forceinline__ uint2 pack_floor_bits_u8(const uint32_t f[8]) {
 constexpr int kDctPairStages = TDCT_DCT_PAIR_STAGES;
 constexpr int kDctPairSlotBytes = 8 * 32 * 16;  // 8 rows x 32 lanes x 16 bytes
 
-// Resident CTAs per SM the pair kernel is compiled for: 3 (168 registers)
-// up to class 21; the larger classes hold more coefficients and run at 2.
-__host__ __device__ constexpr int dct_pair_min_ctas(int R) { return R >= 28 ? 2 : 3; }
+// Resident CTAs per SM the pair kernel is compiled for: 4 (128 registers, no
+// spills) up to class 16 (2 % faster than 3 at r = 16, bench workload), 3 for
+// class 21 (it would spill at 128), 2 from class 28 (more coefficients live).
+__host__ __device__ constexpr int dct_pair_min_ctas(int R) {
+#ifdef TDCT_DCT_PAIR_MINB
+  return R >= 28 ? 2 : TDCT_DCT_PAIR_MINB;
+#else
+  return R >= 28 ? 2 : R >= 21 ? 3 : 4;
+#endif
+}
 
 template <int R>
 __global__ void __launch_bounds__(128, dct_pair_min_ctas(R))
