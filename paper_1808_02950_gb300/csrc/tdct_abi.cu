@@ -282,7 +282,25 @@ PlaneDesc make_desc(const void* img, int64_t pitch, int H, int W, int dtype, int
   return d;
 }
 
-int64_t units_of(const PlaneDesc& d) { return (int64_t)d.nby * d.chunks; }
+// Units of a plane: per block row ceil(nbx / 64), or, for planes whose units
+// run on across block rows (vec16 bit 5), ceil(nbx nby / 64).
+int64_t units_of(const PlaneDesc& d) {
+  if (d.vec16 & 32) return ((int64_t)d.nbx * d.nby + 63) / 64;
+  return (int64_t)d.nby * d.chunks;
+}
+
+// Bulk-copy u8 planes (rows 16-byte aligned) at least 64 blocks wide whose
+// width is not a multiple of 64 blocks take units that run on across block
+// rows (no nearly empty unit at the end of each block row), at r > 10, where
+// the kernel is bound by issue.  Measured on GB300 (512 planes of 1024 x 1040,
+// a third unit of 2 blocks per block row): r = 16 from 0.46 to 0.64 of the
+// HBM peak; at r = 4, bound by memory, from 0.71 to 0.64 (the copies of
+// segments that start inside a row), so the classes up to 10 keep per-row
+// units.
+bool wants_wrap(const PlaneDesc& d) {
+  return d.dtype == TDCT_U8 && (d.vec16 & 4) && !(d.vec16 & 16) && d.nbx >= 64 &&
+         d.nbx % 64 != 0 && d.r > 10;
+}
 
 cudaError_t dispatch_codec_tc(int r, const PlaneTable& tab, unsigned long long* sse,
                               cudaStream_t s, int ctas_per_sm = 0, int tc_variant = 0) {
@@ -452,10 +470,13 @@ struct Group {
   int any_bulk;     // the planes take the bulk-copy ring
   int staged;       // the planes take the staged-copy ring
   int any_shifted;  // bulk planes with rows 8 mod 16 (their own launch; not the tensor engine)
+  int wrap;         // bulk planes with units across block rows (their own launch; not the tensor engine)
 };
 
+// allow_wrap: the launches of this batch run the T1 ring kernels (the units
+// of the generic-T and tensor-core kernels stay per block row).
 int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& descs,
-                std::vector<Group>& groups, std::vector<int64_t>& npix) {
+                std::vector<Group>& groups, std::vector<int64_t>& npix, bool allow_wrap) {
   if (!planes || nplanes < 1 || nplanes > (1 << 20))
     return fail(TDCT_EINVAL, "nplanes = %d outside 1..2^20 (or planes is NULL)", nplanes);
   std::map<std::tuple<int, int, int>, std::vector<int>> by_key;
@@ -470,10 +491,12 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
     if (p.recon && p.recon_pitch < (int64_t)p.W * sample_bytes(p.dtype))
       return fail(TDCT_EINVAL, "plane %d: recon pitch too small", i);
     const PlaneDesc probe = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, p.r, p.recon, p.recon_pitch, i);
-    // load path: 1 bulk-copy ring (3: its 8 mod 16 rows variant), 2 staged, 0 plain
-    by_key[{p.dtype, p.r,
-            (probe.vec16 & 4) ? ((probe.vec16 & 16) ? 3 : 1) : (probe.vec16 & 8) ? 2 : 0}]
-        .push_back(i);
+    // load path: 1 bulk-copy ring (3: its 8 mod 16 rows variant, 4: units
+    // across block rows), 2 staged, 0 plain
+    const int load = (probe.vec16 & 4)
+                         ? ((probe.vec16 & 16) ? 3 : (allow_wrap && wants_wrap(probe)) ? 4 : 1)
+                         : (probe.vec16 & 8) ? 2 : 0;
+    by_key[{p.dtype, p.r, load}].push_back(i);
     npix[i] = (int64_t)p.H * p.W;
   }
   descs.clear();
@@ -481,11 +504,12 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
   for (auto& kv : by_key) {
     const int load = std::get<2>(kv.first);
     Group g{std::get<0>(kv.first), std::get<1>(kv.first), (int)descs.size(),
-            (int)kv.second.size(), 0, (load == 1 || load == 3) ? 1 : 0, load == 2 ? 1 : 0,
-            load == 3 ? 1 : 0};
+            (int)kv.second.size(), 0, (load == 1 || load == 3 || load == 4) ? 1 : 0,
+            load == 2 ? 1 : 0, load == 3 ? 1 : 0, load == 4 ? 1 : 0};
     for (int i : kv.second) {
       const tdct_plane& p = planes[i];
       PlaneDesc d = make_desc(p.img, p.pitch, p.H, p.W, p.dtype, p.r, p.recon, p.recon_pitch, i);
+      if (load == 4) d.vec16 |= 32;
       d.unit_begin = g.units;
       g.units += units_of(d);
       descs.push_back(d);
@@ -493,6 +517,14 @@ int build_batch(const tdct_plane* planes, int nplanes, std::vector<PlaneDesc>& d
     groups.push_back(g);
   }
   return TDCT_OK;
+}
+
+// Whether a batch coded with transform tr on engine `path` may use units
+// across block rows: the T1 ring kernels take them, the generic-T and
+// tensor-core kernels do not (under TDCT_PATH_AUTO such groups run on the
+// butterfly engine whatever the autotuner picks).
+bool wrap_allowed(const Transform& tr, int path) {
+  return tr.t1 && path != TDCT_PATH_TENSOR && path != TDCT_PATH_TENSOR_PIPELINED;
 }
 
 // Enqueue the kernels of a batch whose descriptors live at d_descs (device).
@@ -511,10 +543,11 @@ cudaError_t enqueue_batch(const Transform& tr, const std::vector<Group>& groups,
     tab.any_bulk = g.any_bulk;
     tab.shifted = g.any_shifted;
     tab.staged = g.staged;
+    tab.wrap = g.wrap;
     const bool tensor = path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED;
     if (!tr.t1)
       e = dispatch_codec_generic(g.r, g.dtype, tab, tr, sse, s);
-    else if (tensor && g.any_bulk && !g.any_shifted && g.dtype == TDCT_U8)
+    else if (tensor && g.any_bulk && !g.any_shifted && !g.wrap && g.dtype == TDCT_U8)
       e = dispatch_codec_tc(g.r, tab, sse, s, ctas_per_sm,
                             path == TDCT_PATH_TENSOR_PIPELINED ? 1 : tc_variant);
     else
@@ -717,7 +750,7 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
   std::vector<PlaneDesc> descs;
   std::vector<Group> groups;
   std::vector<int64_t> npix;
-  if ((rc = build_batch(planes, nplanes, descs, groups, npix))) return rc;
+  if ((rc = build_batch(planes, nplanes, descs, groups, npix, wrap_allowed(tr, path)))) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED) {
     const uint16_t* table = nullptr;
@@ -757,7 +790,7 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
   tdct_plan* plan = new (std::nothrow) tdct_plan;
   if (!plan) return fail(TDCT_ENOMEM, "host allocation failed");
   plan->tr = tr;
-  if ((rc = build_batch(planes, nplanes, descs, plan->groups, npix))) {
+  if ((rc = build_batch(planes, nplanes, descs, plan->groups, npix, wrap_allowed(tr, path)))) {
     delete plan;
     return rc;
   }
@@ -1030,7 +1063,8 @@ int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, cons
   std::vector<PlaneDesc> descs;
   std::vector<Group> groups;
   std::vector<int64_t> npix;
-  if ((rc = build_batch(planes, nplanes, descs, groups, npix))) return rc;
+  if ((rc = build_batch(planes, nplanes, descs, groups, npix, wrap_allowed(tr, TDCT_PATH_AUTO))))
+    return rc;
   void* scratch = nullptr;
   if ((rc = noalloc_scratch(&scratch))) return rc;
   PlaneDesc* d_descs = static_cast<PlaneDesc*>(scratch);
@@ -1132,7 +1166,7 @@ int tdct_codec_error_batched_host(const tdct_plane* planes, int nplanes, const i
     }
     std::vector<PlaneDesc> dc;
     std::vector<int64_t> nc;
-    rc = build_batch(staged.data(), count, dc, groups[c], nc);
+    rc = build_batch(staged.data(), count, dc, groups[c], nc, wrap_allowed(tr, TDCT_PATH_AUTO));
     if (rc == TDCT_OK) {
       std::copy(dc.begin(), dc.end(), descs.begin() + first);
       std::copy(nc.begin(), nc.end(), npix.begin() + first);

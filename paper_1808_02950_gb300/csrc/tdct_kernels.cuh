@@ -33,7 +33,8 @@ struct PlaneDesc {
   int32_t vec16;       // bit 0: img rows 8-byte aligned; bit 1: recon rows;
                        // bit 2: u8 plane eligible for the bulk-copy ring;
                        // bit 3: plane eligible for a staged-copy ring (u8 or int16);
-                       // bit 4: bulk-copy plane whose odd rows start 8 mod 16
+                       // bit 4: bulk-copy plane whose odd rows start 8 mod 16;
+                       // bit 5: bulk-copy plane with units across block rows
   int32_t slot;        // output index for SSE / PSNR
   int32_t pad_;
 };
@@ -46,6 +47,7 @@ struct PlaneTable {
   PlaneDesc one;
   int32_t staged;      // the planes take a staged-copy ring (vec16 bit 3)
   int32_t shifted;     // bulk-copy planes with rows 8 mod 16 (vec16 bit 4)
+  int32_t wrap;        // bulk-copy planes whose units run on across block rows (vec16 bit 5)
 };
 
 __device__ __forceinline__ const PlaneDesc& plane_at(const PlaneTable& t, int i) {
@@ -945,7 +947,16 @@ __host__ __device__ constexpr int ring_unit_bytes() {
   return SHIFT ? kRingUnitBytes : kUnitBytes;
 }
 
-template <int R, int STAGES, bool SHIFT = false>
+// WRAP: the launch's planes have units that run on across block rows (64
+// consecutive blocks in raster order; vec16 bit 5): at most two row segments
+// per unit, because such planes are at least 64 blocks wide.  The ring row k
+// of a slot holds row k of segment 0 followed by row k of segment 1 (lanes
+// 0-7 copy the first, lanes 8-15 the second); the segments hold even block
+// counts (the width is a multiple of 16), so the second starts 16-byte
+// aligned in the slot and every pair lies in one block row.  A block row
+// whose width is not a multiple of 64 blocks then leaves no nearly empty unit
+// behind, which at the compute-bound r cost a warp nearly a full unit.
+template <int R, int STAGES, bool SHIFT = false, bool WRAP = false>
 __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
     codec_u8_tma_kernel(const PlaneTable tab, const CodecParams cp,
                         unsigned long long* __restrict__ sse_out) {
@@ -980,6 +991,8 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
   int64_t pp_pitch = 0;
   const uint8_t* pp_img = nullptr;
   int pp_end = -1, pp_W = 0, pp_chunks = 1, pp_by = 0, pp_chunk = 0, pp_s = 0;
+  int64_t pp_rem = 0;  // WRAP: blocks from the unit's first to the plane's end
+  int pp_nbx = 0;      // WRAP: the plane's block columns (pp_chunk is the unit's first one)
   uint32_t issued = 0;  // bit s: slot s holds a copy in flight
   uint32_t phase = 0;   // bit s: parity of slot s's next completion
   int pf = 0;           // next unit to prefetch (from u_begin)
@@ -999,8 +1012,42 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
       const int64_t e = ((q + 1 < tab.n) ? tab.d[q + 1].unit_begin : U) - u_begin;
       pp_end = (int)(e < n_units ? e : n_units);
       const int64_t local = u - Q.unit_begin;
-      pp_by = (int)(local / pp_chunks);
-      pp_chunk = (int)(local - (int64_t)pp_by * pp_chunks);
+      if constexpr (WRAP) {
+        const int64_t blk0 = local * 64;
+        pp_nbx = Q.nbx;
+        pp_by = (int)(blk0 / pp_nbx);
+        pp_chunk = (int)(blk0 - (int64_t)pp_by * pp_nbx);
+        pp_rem = (int64_t)Q.nbx * Q.nby - blk0;
+      } else {
+        pp_by = (int)(local / pp_chunks);
+        pp_chunk = (int)(local - (int64_t)pp_by * pp_chunks);
+      }
+    }
+    if constexpr (WRAP) {
+      const int by0 = pp_by, bx0 = pp_chunk;
+      const int rc = (int)(pp_rem < 64 ? pp_rem : 64);
+      const int n0 = min(rc, pp_nbx - bx0), n1 = rc - n0;
+      pp_rem -= 64;
+      pp_chunk += 64;
+      if (pp_chunk >= pp_nbx) {
+        pp_chunk -= pp_nbx;
+        ++pp_by;
+      }
+      const uint32_t bar = bars + 8 * s;
+      const int k = lane & 7, seg = lane >> 3;  // lanes 0-7: segment 0, 8-15: segment 1
+      const uint8_t* src = seg == 0 ? pp_img + (int64_t)(by0 * 8 + k) * pp_pitch + (int64_t)bx0 * 8
+                                    : pp_img + (int64_t)((by0 + 1) * 8 + k) * pp_pitch;
+      const uint32_t bytes = seg == 0 ? 8u * (uint32_t)n0 : 8u * (uint32_t)n1;
+      const uint32_t dst_off = (uint32_t)k * 512u + (seg == 0 ? 0u : 8u * (uint32_t)n0);
+      // order this warp's earlier generic reads of the slot before the async writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (lane == 0) mbar_arrive_expect_tx(bar, 64u * (uint32_t)rc);
+      __syncwarp();
+      const bool skip = hook && i == 0;
+      if (lane < 16 && bytes > 0 && !skip)
+        bulk_copy_g2s(smem_addr(ring + s * UB + dst_off), src, bytes, bar);
+      issued |= 1u << s;
+      return;
     }
     const int by = pp_by, chunk = pp_chunk;
     if (++pp_chunk == pp_chunks) {
@@ -1053,6 +1100,7 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
   int p_end = -1;
   PlaneDesc P;
   int by = 0, chunk = 0, s = 0;  // consumer cursor, advanced like the producer's
+  int64_t rem = 0;               // WRAP: as pp_rem (chunk: the unit's first block column)
   unsigned long long acc = 0;
   for (int i = 0; i < n_units; ++i) {
     if (i >= p_end) {
@@ -1067,8 +1115,37 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
       const int64_t e = ((p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U) - u_begin;
       p_end = (int)(e < n_units ? e : n_units);
       const int64_t local = u - P.unit_begin;
-      by = (int)(local / P.chunks);
-      chunk = (int)(local - (int64_t)by * P.chunks);
+      if constexpr (WRAP) {
+        const int64_t blk0 = local * 64;
+        by = (int)(blk0 / P.nbx);
+        chunk = (int)(blk0 - (int64_t)by * P.nbx);
+        rem = (int64_t)P.nbx * P.nby - blk0;
+      } else {
+        by = (int)(local / P.chunks);
+        chunk = (int)(local - (int64_t)by * P.chunks);
+      }
+    }
+    if constexpr (WRAP) {
+      // the lane's pair: block 2 lane of the unit, in segment 0 or 1
+      const int rc = (int)(rem < 64 ? rem : 64);
+      const int n0 = min(rc, P.nbx - chunk), pb = 2 * lane;
+      const bool has = pb < rc;
+      const int lby = pb < n0 ? by : by + 1, lbx = pb < n0 ? chunk + pb : pb - n0;
+      const int cur_s = s;
+      rem -= 64;
+      chunk += 64;
+      if (chunk >= P.nbx) {
+        chunk -= P.nbx;
+        ++by;
+      }
+      s = s + 1 == STAGES ? 0 : s + 1;
+      if (!wait_slot(cur_s)) return;
+      const uint8_t* slot = ring + cur_s * UB + lane * 16;
+      if (has)
+        acc += codec_pair_u8<R, true>(P, lby, lbx, RowsInSmem{slot}, RowsInSmem{slot + 8}, cp);
+      __syncwarp();
+      if (pf < n_units) issue_next();  // refill the slot just used
+      continue;
     }
     const int bx0 = chunk * 64 + 2 * lane;
     const int cur_by = by, cur_s = s;
@@ -1547,6 +1624,7 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
   constexpr size_t kSmemShift = (size_t)(kRingThreads / 32) * kStages * (kRingUnitBytes + 8);
   constexpr size_t kSmemStaged = (size_t)(kRingThreads / 32) * kStages * kUnitBytes;
   static int resident = 0, resident_bulk = 0, resident_staged = 0, resident_shift = 0;
+  static int resident_wrap = 0;
   static int sms = 0;
   if (resident == 0) {
     sms = device_sms();
@@ -1577,6 +1655,17 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
           &resident_shift, codec_u8_tma_kernel<R, kStages, true>, kRingThreads, kSmemShift);
       if (e != cudaSuccess) return e;
       if (resident_shift < 1) resident_shift = 1;
+      e = cudaFuncSetAttribute(codec_u8_tma_kernel<R, kStages, false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(codec_u8_tma_kernel<R, kStages, false, true>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &resident_wrap, codec_u8_tma_kernel<R, kStages, false, true>, kRingThreads, kSmem);
+      if (e != cudaSuccess) return e;
+      if (resident_wrap < 1) resident_wrap = 1;
       e = cudaFuncSetAttribute(codec_u8_staged_kernel<R, kStages>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemStaged);
       if (e != cudaSuccess) return e;
@@ -1650,7 +1739,7 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
   }
   const bool bulk = DT == 0 && tab.any_bulk;
   const bool staged = DT == 0 && !bulk && tab.staged;
-  int per_sm = bulk ? (tab.shifted ? resident_shift : resident_bulk)
+  int per_sm = bulk ? (tab.shifted ? resident_shift : tab.wrap ? resident_wrap : resident_bulk)
                    : staged ? resident_staged : resident;
   if (cp.ctas_per_sm > 0 && cp.ctas_per_sm < per_sm) per_sm = cp.ctas_per_sm;
   int64_t grid = (int64_t)per_sm * sms;
@@ -1664,6 +1753,9 @@ cudaError_t launch_codec(const PlaneTable& tab, const CodecParams& cp, unsigned 
       if (tab.shifted)
         codec_u8_tma_kernel<R, kStages, true>
             <<<(unsigned)grid, kRingThreads, kSmemShift, s>>>(tab, cp, sse);
+      else if (tab.wrap)
+        codec_u8_tma_kernel<R, kStages, false, true>
+            <<<(unsigned)grid, kRingThreads, kSmem, s>>>(tab, cp, sse);
       else
         codec_u8_tma_kernel<R, kStages><<<(unsigned)grid, kRingThreads, kSmem, s>>>(tab, cp, sse);
       return cudaGetLastError();
