@@ -507,17 +507,10 @@ def time_ours(args, dist, out):
         jam = {}
         for B in (16, 32):
             T = jam_matrix(B)
-            for _ in range(2):
-                P.tdct_codec_error_jam(big, B, T, wl.desc["r"], jsse, recon=rec_big, stream=stream)
-            torch.cuda.synchronize()
-            j0 = torch.cuda.Event(enable_timing=True)
-            j1 = torch.cuda.Event(enable_timing=True)
-            j0.record(stream)
-            for _ in range(5):
-                P.tdct_codec_error_jam(big, B, T, wl.desc["r"], jsse, recon=rec_big, stream=stream)
-            j1.record(stream)
-            torch.cuda.synchronize()
-            ms = j0.elapsed_time(j1) / 5
+            # 3 untimed and 10 timed launches per B
+            ms = time_launches(lambda: P.tdct_codec_error_jam(big, B, T, wl.desc["r"], jsse,
+                                                              recon=rec_big, stream=stream),
+                               stream, 10)
             gbs = 2 * big.numel() / (ms / 1e3) / 1e9
             jam[f"B{B}"] = {"ms": ms, "r": wl.desc["r"], "pixels_per_s": big.numel() / (ms / 1e3),
                             "hbm_gbs": gbs, "frac_of_measured_hbm": gbs / measured_peaks()[0]}
@@ -532,19 +525,11 @@ def time_ours(args, dist, out):
         dct = {}
         for name, prec in (("fp32", P.TDCT_FP32), ("bf16", P.TDCT_BF16),
                            ("bf16x3", P.TDCT_BF16X3)):
-            for _ in range(2):
-                P.tdct_dct_codec_error(big, wl.desc["r"], dsse, precision=prec, recon=rec_big,
-                                       stream=stream)
-            torch.cuda.synchronize()
-            d0 = torch.cuda.Event(enable_timing=True)
-            d1 = torch.cuda.Event(enable_timing=True)
-            d0.record(stream)
-            for _ in range(5):
-                P.tdct_dct_codec_error(big, wl.desc["r"], dsse, precision=prec, recon=rec_big,
-                                       stream=stream)
-            d1.record(stream)
-            torch.cuda.synchronize()
-            ms = d0.elapsed_time(d1) / 5
+            # 3 untimed and 10 timed launches per precision
+            ms = time_launches(lambda: P.tdct_dct_codec_error(big, wl.desc["r"], dsse,
+                                                              precision=prec, recon=rec_big,
+                                                              stream=stream),
+                               stream, 10)
             blocks = big.numel() // 64
             gbs = 2 * big.numel() / (ms / 1e3) / 1e9
             dct[name] = {"ms": ms, "r": wl.desc["r"], "blocks_per_s": blocks / (ms / 1e3),

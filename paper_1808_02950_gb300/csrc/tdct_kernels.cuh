@@ -1066,7 +1066,9 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
       // rows (base 16-byte aligned, W % 16 == 8, H % 8 == 0)
       off = (uint32_t)(reinterpret_cast<uintptr_t>(src) & 15u);
       bytes = lane < 8 ? ((row_bytes + off + 15u) & ~15u) : 0u;
-      total = __reduce_add_sync(0xffffffffu, bytes);
+      // even rows of a unit start on a boundary, odd rows 8 bytes past one
+      // (an odd multiple of the pitch): four copies of each length
+      total = 4u * (((row_bytes + 15u) & ~15u) + ((row_bytes + 8u + 15u) & ~15u));
     }
     // order this warp's earlier generic reads of the slot before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
