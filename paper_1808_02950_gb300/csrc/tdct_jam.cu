@@ -198,26 +198,31 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   const int nb = nbx * nby;
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-  // the column stage: two lanes per column when the kept extent allows (16x16
-  // blocks; at 32x32 the extra registers cost a resident CTA and the split
-  // measured 2 % slower)
+  // the column stage: two lanes per column when the kept extent allows at
+  // 16x16 blocks (the two branches of the first JAM stage), four at 32x32 u8
+  // blocks (the two branches of the first two stages) with 4 KE <= 32
   constexpr bool kSplit = B == 16 && 2 * KE <= B;
+  constexpr bool kSplit4 = B == 32 && DT == 0 && 4 * KE <= B;
   // The block's KE leading columns, stored column by column (a column is
   // contiguous, so the column stage moves it with 16-byte accesses): column c
-  // at c * kS, entry of row i at pos(i), where the split stage mirrors the
-  // lower half (rows B - 1 - m at B/2 + m) so that each lane of a column pair
-  // owns one contiguous half.  kS pads a column by 16 bytes; the blocks of a
+  // at c * kS, entry of row i at pos(i), where the split stages order the rows
+  // so that each lane of a column's pair (quad) owns one contiguous half
+  // (quarter) of the outputs: two lanes, rows 0..15 then 31 down to 16; four
+  // lanes, rows 0..7, 15 down to 8, 31 down to 24, 16..23.  kS pads a column by 16 bytes; the blocks of a
   // warp sit 16 banks apart (row accesses of the two halves do not collide).
   constexpr int kEl = (int)sizeof(TileT);
   constexpr int kS = B + 16 / kEl;
   constexpr int kBlkWords = KE * kS * kEl / 4;
   constexpr int kBlk = (KE * kS + ((16 - kBlkWords % 32 + 32) % 32) * 4 / kEl);
   __shared__ __align__(16) TileT tile[4][NP][BPW][kBlk];
-  const int pk_ = (kSplit && k >= B / 2) ? (3 * B / 2 - 1 - k) : k;  // pos(k)
+  const int pk_ = kSplit4 ? (k < 8 ? k : k < 16 ? 23 - k : k < 24 ? k + 8 : 47 - k)
+                  : (kSplit && k >= B / 2) ? (3 * B / 2 - 1 - k) : k;  // pos(k)
   constexpr uint32_t kBlockMask = (2 * KE >= 32) ? 0xffffffffu : ((1u << (2 * KE)) - 1u);
   constexpr uint32_t kSplitMask = B == 16 ? (kBlockMask | (kBlockMask << 16)) : kBlockMask;
-  // kept rows of the lane's column in the column stage
-  const int hk = kept_height(B, jp.r, kSplit ? (k >> 1) : k);
+  constexpr uint32_t kQuadMask = (4 * KE >= 32) ? 0xffffffffu : ((1u << (4 * KE)) - 1u);
+  // the lane's column in the column stage and its kept rows
+  const int ccol = kSplit4 ? (k >> 2) : kSplit ? (k >> 1) : k;
+  const int hk = kept_height(B, jp.r, ccol);
   // rounding bias folded into the DC input of the row inverse (T's first row
   // is all ones, so it reaches every output): L^2 for u8 samples; int16
   // residuals round half away from zero on |2N| instead
@@ -229,12 +234,13 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
   // takes V'[k][c] q_c straight from the tile; products wrap mod 2^32, the
   // result does not).
   constexpr bool kFoldQ = kStageB32<B, DT>;
-  constexpr int kNQ = kSplit ? KE / 2 : KE;
+  constexpr int kNQ = kSplit4 ? (KE + 3) / 4 : kSplit ? KE / 2 : KE;
   constexpr int kNQR = kNQ <= 8 ? kNQ : 1;
   int32_t qm2r[kNQR];
-  const int qc = kFoldQ ? jp.q[min(kSplit ? (k >> 1) : k, KE - 1)] : 1;
+  const int qc = kFoldQ ? jp.q[min(ccol, KE - 1)] : 1;
   auto qm2_of = [&](int i) {
-    const int ifull = kSplit ? 2 * i + (k & 1) : i;
+    // the row of Z that output i of the lane's last-stage forward is
+    const int ifull = kSplit4 ? 4 * i + (k & 3) : kSplit ? 2 * i + (k & 1) : i;
     return ifull < hk ? (int32_t)((uint32_t)(2 * jp.q[ifull]) * (uint32_t)qc) : 0;
   };
 #pragma unroll
@@ -410,6 +416,33 @@ __global__ void __launch_bounds__(128) jam_codec_kernel(const PlaneDesc P, const
             val[m] = pm + (rh[m] ^ hm) - hm;
           }
           col_store<TileT, B / 2>(tl + c * kS + (k & 1) * (B / 2), val);
+        }
+      } else if constexpr (kSplit4) {
+        // four lanes per column: lane bit 0 picks the branch of the first JAM
+        // stage (sums x_m + x_(31-m) or differences), bit 1 that of the
+        // second on the resulting 16-point signal; each lane runs the 8-point
+        // forward (Z rows 4 i + (k & 3)), the mask and the 8-point inverse, and
+        // two exchanges (lane ^ 2, then lane ^ 1) rebuild the 16- and
+        // 32-point inverses, a quarter of the column per lane
+        if (k < 4 * KE) {
+          const int c = k >> 2;
+          const uint32_t s1 = (k & 1) ? 0xffffffffu : 1u, s2 = (k & 2) ? 0xffffffffu : 1u;
+          uint32_t col[B], y8[8], z8[8];
+          col_load<TileT, B>(tl + c * kS, col);  // rows 0..7, 15..8, 31..24, 16..23
+  #pragma unroll
+          for (int m = 0; m < 8; ++m)
+            y8[m] = (col[m] + s1 * col[16 + m]) + s2 * (col[8 + m] + s1 * col[24 + m]);
+          jam_fwd<8, uint32_t>(y8, z8);
+          VA w[8], r8[8];
+  #pragma unroll
+          for (int i = 0; i < 8; ++i) w[i] = i < kNQ ? (VA)(z8[i] * (uint32_t)qm2(i)) : (VA)0;
+          jam_inv<8, VA>(w, r8);
+          VA v2[8], v1[8];
+  #pragma unroll
+          for (int m = 0; m < 8; ++m) v2[m] = __shfl_xor_sync(kQuadMask, r8[m], 2) + s2 * r8[m];
+  #pragma unroll
+          for (int m = 0; m < 8; ++m) v1[m] = __shfl_xor_sync(kQuadMask, v2[m], 1) + s1 * v2[m];
+          col_store<TileT, 8>(tl + c * kS + 8 * (2 * (k & 1) + ((k >> 1) & 1)), v1);
         }
       } else if (k < KE) {
         uint32_t col[B], z[B];
