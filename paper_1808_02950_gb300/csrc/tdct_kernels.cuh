@@ -275,6 +275,12 @@ __device__ __forceinline__ uint32_t min_relu_s16x2(uint32_t a, uint32_t b) {
   return d;
 }
 
+// Lanes of a packed word a + 2^16 b (a, b in [-2^15, 2^15)).
+__device__ __forceinline__ int32_t lane_lo(uint32_t v) { return (int32_t)(int16_t)(v & 0xffffu); }
+__device__ __forceinline__ int32_t lane_hi(uint32_t v) {
+  return (int32_t)(v - (uint32_t)lane_lo(v)) >> 16;
+}
+
 // ---- int16 residual path: one block at a time, epilogue streamed by rows ------
 //
 // Residuals reach |Z| = 36720 (> int16), so the forward is per block in int32.
@@ -306,21 +312,13 @@ struct I16RowsInSmem {
   }
 };
 
+// Inverse, rounding, SSE and store of one int16 block from its kept, scaled
+// coefficients w (doubled multipliers; samples re-read through rw).
 template <int R, typename RS>
-__device__ __forceinline__ uint32_t codec_block_i16(const PlaneDesc& P, int by, int bx, RS rw,
-                                                    const CodecParams& cp, int valid_rows,
-                                                    int valid_cols) {
+__device__ __forceinline__ uint32_t inverse_epilogue_i16(const uint32_t w[64], const PlaneDesc& P,
+                                                         int by, int bx, RS rw, int valid_rows,
+                                                         int valid_cols) {
   const bool full = valid_rows == 8 && valid_cols == 8;
-  uint32_t w[64];
-  {
-    uint32_t x[64], z[64];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) unpack_i16x8(rw.row(k), x + 8 * k);
-    fwd2d<uint32_t>(x, z);
-#pragma unroll
-    for (int p = 0; p < 64; ++p)
-      w[p] = kept(R, p / 8, p % 8) ? z[p] * (uint32_t)cp.cmul2[p] : 0u;
-  }
   // columns first: v[k][j] = sum_i t_i[k] w[i][j]
   uint32_t v[64];
 #pragma unroll
@@ -374,6 +372,140 @@ __device__ __forceinline__ uint32_t codec_block_i16(const PlaneDesc& P, int by, 
     }
   }
   return acc;
+}
+
+template <int R, typename RS>
+__device__ __forceinline__ uint32_t codec_block_i16(const PlaneDesc& P, int by, int bx, RS rw,
+                                                    const CodecParams& cp, int valid_rows,
+                                                    int valid_cols) {
+  uint32_t w[64];
+  {
+    uint32_t x[64], z[64];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) unpack_i16x8(rw.row(k), x + 8 * k);
+    fwd2d<uint32_t>(x, z);
+#pragma unroll
+    for (int p = 0; p < 64; ++p)
+      w[p] = kept(R, p / 8, p % 8) ? z[p] * (uint32_t)cp.cmul2[p] : 0u;
+  }
+  return inverse_epilogue_i16<R>(w, P, by, bx, rw, valid_rows, valid_cols);
+}
+
+// Classes whose kept coefficients all fit 16-bit lanes for int16 residuals
+// (|x| <= 255) except possibly Z_22: with the row sums of |T1| (8, 10, 12, 10,
+// 8, 10, 12, 10), |Z_ij| <= 255 * 120 < 2^15 unless both i and j are 2 or 6
+// (36720); up to class 36 only (2, 2) is kept among those, and it is formed
+// separately in 32 bits.  Used up to class 32 (class 36 would spill).
+template <int R>
+__host__ __device__ constexpr bool i16_packed_forward() {
+#ifdef TDCT_I16_PACKED
+  return TDCT_I16_PACKED && R <= 32;
+#else
+  return R <= 32;
+#endif
+}
+
+// The lane's two int16 blocks (A at slot, B at slot + 16; rows 1024 bytes
+// apart) through one packed forward (a + 2^16 b per word), then each block's
+// inverse.  Samples enter biased by 2^15 (x ^ 0x8000 per lane: unsigned 16-bit
+// lanes, packed by one byte permute), which only moves Z_00, by 64 * 2^15 per
+// lane (2^21 in the packed word, mod 2^32); Z_22 of classes that keep it is
+// evaluated per block from the first pass's column (or row) 2.
+template <int R>
+__device__ __forceinline__ uint32_t codec_pair_i16(const PlaneDesc& P, int by, int bx0,
+                                                   const uint8_t* slot, const CodecParams& cp,
+                                                   int valid_rows, bool has1) {
+  uint32_t z[64];
+  int32_t z22[2] = {0, 0};
+  {
+    uint32_t pk[64], t[64];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint4 a = *reinterpret_cast<const uint4*>(slot + k * 1024);
+      const uint4 b = *reinterpret_cast<const uint4*>(slot + 16 + k * 1024);
+      const uint32_t aw[4] = {a.x ^ 0x80008000u, a.y ^ 0x80008000u, a.z ^ 0x80008000u,
+                              a.w ^ 0x80008000u};
+      const uint32_t bw[4] = {b.x ^ 0x80008000u, b.y ^ 0x80008000u, b.z ^ 0x80008000u,
+                              b.w ^ 0x80008000u};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        pk[8 * k + 2 * m] = __byte_perm(aw[m], bw[m], 0x5410u);
+        pk[8 * k + 2 * m + 1] = __byte_perm(aw[m], bw[m], 0x7632u);
+      }
+    }
+    constexpr bool kFix = kept(R, 2, 2);
+    if constexpr (kept_cols(R) <= kept_rows(R)) {
+      // rows first: t[k][j], then the kept positions of each column
+#pragma unroll
+      for (int k = 0; k < 8; ++k) fwd8<uint32_t>(pk + 8 * k, t + 8 * k);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t col[8], o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) col[k] = t[8 * k + j];
+        fwd8<uint32_t>(col, o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[8 * i + j] = o[i];
+      }
+      if constexpr (kFix) {
+        // Z_22 = sum_k T1[2][k] t[k][2] per block (|t| <= 12 * 255: exact lanes)
+        uint32_t ca[8], cb[8], oa[8], ob[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          ca[k] = (uint32_t)lane_lo(t[8 * k + 2]);
+          cb[k] = (uint32_t)lane_hi(t[8 * k + 2]);
+        }
+        fwd8<uint32_t>(ca, oa);
+        fwd8<uint32_t>(cb, ob);
+        z22[0] = (int32_t)oa[2];
+        z22[1] = (int32_t)ob[2];
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        uint32_t col[8], o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) col[k] = pk[8 * k + l];
+        fwd8<uint32_t>(col, o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[8 * i + l] = o[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) fwd8<uint32_t>(t + 8 * i, z + 8 * i);
+      if constexpr (kFix) {
+        uint32_t ra[8], rb[8], oa[8], ob[8];
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+          ra[l] = (uint32_t)lane_lo(t[16 + l]);
+          rb[l] = (uint32_t)lane_hi(t[16 + l]);
+        }
+        fwd8<uint32_t>(ra, oa);
+        fwd8<uint32_t>(rb, ob);
+        z22[0] = (int32_t)oa[2];
+        z22[1] = (int32_t)ob[2];
+      }
+    }
+    z[0] -= 2097152u;  // the 2^15 bias of both lanes: 64 * 2^15 (1 + 2^16) mod 2^32
+  }
+  uint32_t sse = 0;
+#pragma unroll 1
+  for (int b = 0; b < 2; ++b) {
+    if (b == 1 && !has1) break;
+    uint32_t w[64];
+#pragma unroll
+    for (int p = 0; p < 64; ++p) {
+      const int i = p / 8, j = p % 8;
+      if (!kept(R, i, j)) {
+        w[p] = 0u;
+        continue;
+      }
+      int32_t zz = b == 0 ? lane_lo(z[p]) : lane_hi(z[p]);
+      if (i == 2 && j == 2) zz = z22[b];
+      w[p] = (uint32_t)zz * (uint32_t)cp.cmul2[p];
+    }
+    sse += inverse_epilogue_i16<R>(w, P, by, bx0 + b, I16RowsInSmem{slot + 16 * b}, valid_rows, 8);
+  }
+  return sse;
 }
 
 // The lane's two int16 blocks (bx0, bx0 + 1) of block-row `by`, one after the
@@ -435,10 +567,6 @@ __device__ __forceinline__ void pair_row(uint2 a, uint2 b, uint32_t p[8]) {
   p[7] = __byte_perm(a57, b.y, 0x1712u);
 }
 
-__device__ __forceinline__ int32_t lane_lo(uint32_t v) { return (int32_t)(int16_t)(v & 0xffffu); }
-__device__ __forceinline__ int32_t lane_hi(uint32_t v) {
-  return (int32_t)(v - (uint32_t)lane_lo(v)) >> 16;
-}
 
 // Round, clamp and pack one row of 8 doubled-and-biased inverse values.
 __device__ __forceinline__ uint2 round_pack_row_u8(const uint32_t n2[8]) {
@@ -1592,11 +1720,16 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, 3)
       __syncwarp();
     }
     const uint8_t* slot = slot_all + lane * 32;
+    if constexpr (i16_packed_forward<R>()) {
+      if (bx0 < P.nbx)
+        acc += codec_pair_i16<R>(P, cur_by, bx0, slot, cp, valid_rows, bx0 + 1 < P.nbx);
+    } else {
 #pragma unroll 1
-    for (int b = 0; b < 2; ++b) {
-      if (bx0 + b < P.nbx)
-        acc += codec_block_i16<R>(P, cur_by, bx0 + b, I16RowsInSmem{slot + 16 * b}, cp, valid_rows,
-                                  8);
+      for (int b = 0; b < 2; ++b) {
+        if (bx0 + b < P.nbx)
+          acc += codec_block_i16<R>(P, cur_by, bx0 + b, I16RowsInSmem{slot + 16 * b}, cp,
+                                    valid_rows, 8);
+      }
     }
     __syncwarp();
     if (pf < n_units) issue_next();  // refill the slot just used

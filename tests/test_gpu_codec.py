@@ -512,3 +512,37 @@ def test_autotuned_plan_is_correct_and_reports_its_choice():
         assert int(sse[i]) == want_sse
         assert np.array_equal(recons[i].cpu().numpy(), want_rec)
     plan.close()
+
+
+def _extreme_i16_blocks():
+    """int16 blocks at the residual bound: constants +-255 and +-255 times the
+    sign pattern of every basis image t_i t_j^T of T1 (the inputs that
+    maximise |Z_ij|), side by side in one 8-row strip."""
+    T = np.array(M.T1, dtype=np.int64)
+    blocks = [np.full((8, 8), 255), np.full((8, 8), -255)]
+    for i in range(8):
+        for j in range(8):
+            sgn = np.sign(np.outer(T[i], T[j]))
+            sgn[sgn == 0] = 1
+            blocks.append(255 * sgn)
+            blocks.append(-255 * sgn)
+    return np.concatenate(blocks, axis=1).astype(np.int16)
+
+
+@pytest.mark.parametrize("r", [1, 8, 10, 12, 13, 15, 16, 21, 28, 32, 36, 45, 64])
+def test_int16_bulk_ring_extreme_blocks(r):
+    """The int16 bulk-copy ring (two blocks per lane through a 16-bit packed
+    forward up to class 32, Z_22 in 32 bits) on the blocks that reach the
+    coefficient bounds, bit-exact against the oracle."""
+    host = _extreme_i16_blocks()
+    H, W = host.shape  # 8 x 8 * 130 (W % 8 == 0, rows 16-byte aligned)
+    view = torch.from_numpy(host).to(DEV)
+    for hh in (8, 16):
+        h = np.ascontiguousarray(np.concatenate([host] * (hh // 8), axis=0)[:, ::-1])
+        v = torch.from_numpy(h).to(DEV)
+        sse, rec, _ = run_codec(v, r)
+        want_sse, want_rec, _ = oc.codec_plane(h, M.T1, r)
+        assert sse == want_sse and np.array_equal(rec, want_rec), (r, hh)
+    sse, rec, _ = run_codec(view, r)
+    want_sse, want_rec, _ = oc.codec_plane(host, M.T1, r)
+    assert sse == want_sse and np.array_equal(rec, want_rec), r
