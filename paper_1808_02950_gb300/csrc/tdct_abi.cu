@@ -527,14 +527,34 @@ bool wrap_allowed(const Transform& tr, int path) {
   return tr.t1 && path != TDCT_PATH_TENSOR && path != TDCT_PATH_TENSOR_PIPELINED;
 }
 
+// Streams on which the groups of a plan's graph run side by side (so that
+// one group's launch tail overlaps the next group's start).
+constexpr int kPlanBranches = 4;
+struct Branches {
+  cudaStream_t stream[kPlanBranches] = {};
+  cudaEvent_t fork = nullptr, join[kPlanBranches] = {};
+};
+
 // Enqueue the kernels of a batch whose descriptors live at d_descs (device).
+// With `br`, the groups are distributed round-robin over its streams between a
+// fork and a join on s (graph capture: parallel branches).
 cudaError_t enqueue_batch(const Transform& tr, const std::vector<Group>& groups,
                           const PlaneDesc* d_descs, const int64_t* d_npix, int nplanes,
                           unsigned long long* sse, double* psnr, cudaStream_t s,
-                          int path = TDCT_PATH_AUTO, int ctas_per_sm = 0, int tc_variant = 0) {
+                          int path = TDCT_PATH_AUTO, int ctas_per_sm = 0, int tc_variant = 0,
+                          const Branches* br = nullptr) {
   cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long) * nplanes, s);
   if (e != cudaSuccess) return e;
+  const int nbr = (br && groups.size() > 1) ? (int)std::min<size_t>(groups.size(), kPlanBranches) : 0;
+  if (nbr > 0) {
+    if ((e = cudaEventRecord(br->fork, s)) != cudaSuccess) return e;
+    for (int b = 0; b < nbr; ++b)
+      if ((e = cudaStreamWaitEvent(br->stream[b], br->fork, 0)) != cudaSuccess) return e;
+  }
+  int gi = 0;
   for (const Group& g : groups) {
+    const cudaStream_t gs = nbr > 0 ? br->stream[gi % nbr] : s;
+    ++gi;
     PlaneTable tab;
     std::memset(&tab, 0, sizeof tab);
     tab.d = d_descs + g.first;
@@ -546,13 +566,17 @@ cudaError_t enqueue_batch(const Transform& tr, const std::vector<Group>& groups,
     tab.wrap = g.wrap;
     const bool tensor = path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED;
     if (!tr.t1)
-      e = dispatch_codec_generic(g.r, g.dtype, tab, tr, sse, s);
+      e = dispatch_codec_generic(g.r, g.dtype, tab, tr, sse, gs);
     else if (tensor && g.any_bulk && !g.any_shifted && !g.wrap && g.dtype == TDCT_U8)
-      e = dispatch_codec_tc(g.r, tab, sse, s, ctas_per_sm,
+      e = dispatch_codec_tc(g.r, tab, sse, gs, ctas_per_sm,
                             path == TDCT_PATH_TENSOR_PIPELINED ? 1 : tc_variant);
     else
-      e = dispatch_codec(g.r, g.dtype, tab, sse, 0, s, ctas_per_sm);
+      e = dispatch_codec(g.r, g.dtype, tab, sse, 0, gs, ctas_per_sm);
     if (e != cudaSuccess) return e;
+  }
+  for (int b = 0; b < nbr; ++b) {
+    if ((e = cudaEventRecord(br->join[b], br->stream[b])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(s, br->join[b], 0)) != cudaSuccess) return e;
   }
   if (psnr) {
     psnr_kernel<<<(nplanes + 255) / 256, 256, 0, s>>>(sse, d_npix, 0, psnr, nplanes);
@@ -579,6 +603,8 @@ struct tdct_plan {
   PlaneDesc* d_descs = nullptr;
   int64_t* d_npix = nullptr;
   cudaStream_t capture_stream = nullptr;
+  Branches branches;           // the groups' parallel branches in the graph (2+ groups)
+  bool has_branches = false;
   cudaGraphExec_t exec = nullptr;
   unsigned long long* exec_sse = nullptr;
   double* exec_psnr = nullptr;
@@ -816,6 +842,14 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
     e = cudaMemcpy(plan->d_npix, npix.data(), sizeof(int64_t) * npix.size(),
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && plan->groups.size() > 1) {
+    plan->has_branches = true;
+    e = cudaEventCreateWithFlags(&plan->branches.fork, cudaEventDisableTiming);
+    for (int b = 0; b < kPlanBranches && e == cudaSuccess; ++b) {
+      e = cudaStreamCreateWithFlags(&plan->branches.stream[b], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->branches.join[b], cudaEventDisableTiming);
+    }
+  }
   if (e != cudaSuccess) {
     tdct_plan_destroy(plan);
     return cuda_fail(e, "tdct_plan_create");
@@ -878,7 +912,8 @@ int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stre
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     const cudaError_t ee = enqueue_batch(plan->tr, plan->groups, plan->d_descs, plan->d_npix,
                                          plan->nplanes, sse, d_psnr, plan->capture_stream,
-                                         plan->path, plan->ctas_per_sm, plan->tc_variant);
+                                         plan->path, plan->ctas_per_sm, plan->tc_variant,
+                                         plan->has_branches ? &plan->branches : nullptr);
     e = cudaStreamEndCapture(plan->capture_stream, &graph);
     if (ee != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -902,6 +937,11 @@ void tdct_plan_destroy(tdct_plan* plan) {
   if (!plan) return;
   if (plan->exec) cudaGraphExecDestroy(plan->exec);
   if (plan->capture_stream) cudaStreamDestroy(plan->capture_stream);
+  for (int b = 0; b < kPlanBranches; ++b) {
+    if (plan->branches.stream[b]) cudaStreamDestroy(plan->branches.stream[b]);
+    if (plan->branches.join[b]) cudaEventDestroy(plan->branches.join[b]);
+  }
+  if (plan->branches.fork) cudaEventDestroy(plan->branches.fork);
   if (plan->d_descs) cudaFree(plan->d_descs);
   if (plan->d_npix) cudaFree(plan->d_npix);
   delete plan;
