@@ -174,12 +174,12 @@ int tdct_codec_error_batched(const tdct_plane* planes, int nplanes, const int8_t
  *   (the same kernels run), except that nplanes above TDCT_NOALLOC_MAX_PLANES
  *   returns TDCT_EINVAL.  No device memory is allocated or freed.
  *   The first call on a device looks up the array's device address (once
- *   per device, with that device current); make that first call before any
- *   stream capture.  Every call rewrites the shared array: calls whose work
- *   overlaps on the GPU (for example on two streams) race on it and must be
- *   serialised by the caller.  Calls from several host threads enqueue their
- *   table copy and kernels under one library lock, so their enqueues never
- *   interleave; the GPU-side rule above still applies.
+ *   per device, with that device current).  Every call rewrites the shared
+ *   array: calls whose work overlaps on the GPU (for example on two streams)
+ *   race on it and must be serialised by the caller.  Calls from several
+ *   host threads enqueue their table copy and kernels under one library
+ *   lock, so their enqueues never interleave; the GPU-side rule above still
+ *   applies.
  */
 #define TDCT_NOALLOC_MAX_PLANES 2048
 int tdct_codec_error_batched_noalloc(const tdct_plane* planes, int nplanes, const int8_t T[64],
