@@ -470,7 +470,7 @@ def time_ours(args, dist, out):
     # MSSIM of every image against its reconstruction (the third figure of
     # merit of the paper's image experiment), timed separately: FP32 work on
     # the CUDA cores, reported against the FP32 FMA peak from unit counts and
-    # clocks (152 SMs x 128 lanes x 2 FLOP x max SM clock).
+    # clocks (the device's SMs x 128 lanes x 2 FLOP x max SM clock).
     u8_planes = [(pl, rc) for (pl, _), rc in zip(wl.planes, wl.recons) if pl.dtype == torch.uint8]
     if not args.no_ssim and u8_planes:
         plan.launch(sse, psnr, stream)  # reconstructions of the timed configuration
