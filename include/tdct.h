@@ -352,9 +352,17 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
 /* The configuration a plan uses: engine (tdct_path), CTAs per SM (0 = the
  * library default) and, for autotuned plans, the tuned step time in ms. */
 int tdct_plan_config(const tdct_plan* plan, int* path, int* ctas_per_sm, float* tuned_ms);
-/* Enqueue one run of the plan on `stream`: SSE (and PSNR) for every plane. */
+/* Enqueue one run of the plan on `stream`: SSE (and PSNR) for every plane.
+ * When every group of the plan runs the u8 bulk-copy ring kernel (T1, u8
+ * planes with 16-byte aligned rows, the butterfly engine), the graph holds
+ * only the codec launches: the warp that finishes a plane's last units
+ * writes its SSE and PSNR from per-plane accumulators the plan owns and
+ * leaves them at zero.  Launches of one plan therefore must not overlap on
+ * the GPU (launches on one stream never do).  Otherwise the graph resets
+ * d_sse, runs the codec launches and a PSNR kernel. */
 int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stream_t stream);
-/* Kernel launches one tdct_plan_launch performs (for launch accounting). */
+/* Kernel launches one tdct_plan_launch performs (for launch accounting):
+ * one per group, plus the PSNR kernel unless the launches close themselves. */
 int tdct_plan_kernel_count(const tdct_plan* plan);
 
 /*

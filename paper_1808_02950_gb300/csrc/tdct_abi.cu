@@ -331,9 +331,17 @@ cudaError_t dispatch_codec_generic(int r, int dtype, const PlaneTable& tab, cons
   }
 }
 
+// fin_cnt (plans whose launches all run the u8 bulk-copy ring kernel): the
+// kernel closes each plane itself (sse is then the plan's accumulator; see
+// CodecParams::fin_cnt).
 cudaError_t dispatch_codec(int r, int dtype, const PlaneTable& tab, unsigned long long* sse,
-                           int max_ctas, cudaStream_t s, int ctas_per_sm = 0) {
-  const CodecParams cp = make_params(r, ctas_per_sm);
+                           int max_ctas, cudaStream_t s, int ctas_per_sm = 0,
+                           unsigned long long* fin_sse = nullptr, double* fin_psnr = nullptr,
+                           unsigned int* fin_cnt = nullptr) {
+  CodecParams cp = make_params(r, ctas_per_sm);
+  cp.fin_sse = fin_sse;
+  cp.fin_psnr = fin_psnr;
+  cp.fin_cnt = fin_cnt;
   switch (r_class(r)) {
 #define TDCT_CASE(R)                                                     \
   case R:                                                                \
@@ -527,6 +535,20 @@ bool wrap_allowed(const Transform& tr, int path) {
   return tr.t1 && path != TDCT_PATH_TENSOR && path != TDCT_PATH_TENSOR_PIPELINED;
 }
 
+// Whether group g of a batch coded with transform tr on engine `path` runs
+// the u8 bulk-copy ring kernel (the kernel that can close its planes itself).
+bool group_on_u8_ring(const Transform& tr, const Group& g, int path) {
+  const bool tensor = path == TDCT_PATH_TENSOR || path == TDCT_PATH_TENSOR_PIPELINED;
+  return tr.t1 && g.dtype == TDCT_U8 && g.any_bulk && !(tensor && !g.any_shifted && !g.wrap);
+}
+
+// A plan's accumulators for launches that close their planes themselves:
+// SSE and finished units per plane (both zero between launches).
+struct PlanFinal {
+  unsigned long long* acc;
+  unsigned int* cnt;
+};
+
 // Streams on which the groups of a plan's graph run side by side (so that
 // one group's launch tail overlaps the next group's start).
 constexpr int kPlanBranches = 4;
@@ -537,14 +559,22 @@ struct Branches {
 
 // Enqueue the kernels of a batch whose descriptors live at d_descs (device).
 // With `br`, the groups are distributed round-robin over its streams between a
-// fork and a join on s (graph capture: parallel branches).
+// fork and a join on s (graph capture: parallel branches).  With `fin` (every
+// group on the u8 bulk-copy ring), the codec launches write SSE and PSNR
+// themselves: no reset of `sse` before them and no PSNR kernel after.
 cudaError_t enqueue_batch(const Transform& tr, const std::vector<Group>& groups,
                           const PlaneDesc* d_descs, const int64_t* d_npix, int nplanes,
                           unsigned long long* sse, double* psnr, cudaStream_t s,
                           int path = TDCT_PATH_AUTO, int ctas_per_sm = 0, int tc_variant = 0,
-                          const Branches* br = nullptr) {
-  cudaError_t e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long) * nplanes, s);
-  if (e != cudaSuccess) return e;
+                          const Branches* br = nullptr, const PlanFinal* fin = nullptr) {
+  cudaError_t e = cudaSuccess;
+  if (fin) {
+    for (const Group& g : groups)
+      if (!group_on_u8_ring(tr, g, path)) return cudaErrorInvalidValue;
+  } else {
+    e = cudaMemsetAsync(sse, 0, sizeof(unsigned long long) * nplanes, s);
+    if (e != cudaSuccess) return e;
+  }
   const int nbr = (br && groups.size() > 1) ? (int)std::min<size_t>(groups.size(), kPlanBranches) : 0;
   if (nbr > 0) {
     if ((e = cudaEventRecord(br->fork, s)) != cudaSuccess) return e;
@@ -570,6 +600,8 @@ cudaError_t enqueue_batch(const Transform& tr, const std::vector<Group>& groups,
     else if (tensor && g.any_bulk && !g.any_shifted && !g.wrap && g.dtype == TDCT_U8)
       e = dispatch_codec_tc(g.r, tab, sse, gs, ctas_per_sm,
                             path == TDCT_PATH_TENSOR_PIPELINED ? 1 : tc_variant);
+    else if (fin)
+      e = dispatch_codec(g.r, g.dtype, tab, fin->acc, 0, gs, ctas_per_sm, sse, psnr, fin->cnt);
     else
       e = dispatch_codec(g.r, g.dtype, tab, sse, 0, gs, ctas_per_sm);
     if (e != cudaSuccess) return e;
@@ -578,7 +610,7 @@ cudaError_t enqueue_batch(const Transform& tr, const std::vector<Group>& groups,
     if ((e = cudaEventRecord(br->join[b], br->stream[b])) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(s, br->join[b], 0)) != cudaSuccess) return e;
   }
-  if (psnr) {
+  if (psnr && !fin) {
     psnr_kernel<<<(nplanes + 255) / 256, 256, 0, s>>>(sse, d_npix, 0, psnr, nplanes);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -605,6 +637,7 @@ struct tdct_plan {
   cudaStream_t capture_stream = nullptr;
   Branches branches;           // the groups' parallel branches in the graph (2+ groups)
   bool has_branches = false;
+  PlanFinal fin{nullptr, nullptr};  // accumulators of launches that close themselves
   cudaGraphExec_t exec = nullptr;
   unsigned long long* exec_sse = nullptr;
   double* exec_psnr = nullptr;
@@ -832,6 +865,10 @@ int tdct_plan_create(const tdct_plane* planes, int nplanes, const int8_t T[64],
   }
   cudaError_t e = cudaMalloc(&plan->d_descs, sizeof(PlaneDesc) * descs.size());
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_npix, sizeof(int64_t) * npix.size());
+  if (e == cudaSuccess) e = cudaMalloc(&plan->fin.acc, sizeof(unsigned long long) * nplanes);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->fin.cnt, sizeof(unsigned int) * nplanes);
+  if (e == cudaSuccess) e = cudaMemset(plan->fin.acc, 0, sizeof(unsigned long long) * nplanes);
+  if (e == cudaSuccess) e = cudaMemset(plan->fin.cnt, 0, sizeof(unsigned int) * nplanes);
   if (e != cudaSuccess) {
     tdct_plan_destroy(plan);
     return fail(TDCT_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
@@ -891,8 +928,23 @@ int tdct_plan_groups(const tdct_plan* plan, tdct_plan_group* out, int max, int* 
   return TDCT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Whether every launch of the plan runs the u8 bulk-copy ring kernel, which
+// then writes SSE and PSNR itself (one kernel node per group, nothing else).
+bool plan_self_closing(const tdct_plan* plan) {
+  for (const Group& g : plan->groups)
+    if (!group_on_u8_ring(plan->tr, g, plan->path)) return false;
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
 int tdct_plan_kernel_count(const tdct_plan* plan) {
-  return plan ? (int)plan->groups.size() + 1 : 0;
+  if (!plan) return 0;
+  return (int)plan->groups.size() + (plan_self_closing(plan) ? 0 : 1);
 }
 
 int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stream_t stream) {
@@ -913,7 +965,8 @@ int tdct_plan_launch(tdct_plan* plan, uint64_t* d_sse, double* d_psnr, tdct_stre
     const cudaError_t ee = enqueue_batch(plan->tr, plan->groups, plan->d_descs, plan->d_npix,
                                          plan->nplanes, sse, d_psnr, plan->capture_stream,
                                          plan->path, plan->ctas_per_sm, plan->tc_variant,
-                                         plan->has_branches ? &plan->branches : nullptr);
+                                         plan->has_branches ? &plan->branches : nullptr,
+                                         plan_self_closing(plan) ? &plan->fin : nullptr);
     e = cudaStreamEndCapture(plan->capture_stream, &graph);
     if (ee != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -944,6 +997,8 @@ void tdct_plan_destroy(tdct_plan* plan) {
   if (plan->branches.fork) cudaEventDestroy(plan->branches.fork);
   if (plan->d_descs) cudaFree(plan->d_descs);
   if (plan->d_npix) cudaFree(plan->d_npix);
+  if (plan->fin.acc) cudaFree(plan->fin.acc);
+  if (plan->fin.cnt) cudaFree(plan->fin.cnt);
   delete plan;
 }
 

@@ -165,6 +165,14 @@ struct CodecParams {
   int32_t ctas_per_sm;   // > 0: cap on resident CTAs per SM (launch tuning)
   int32_t tc_variant;    // tensor engine: 0 one tile at a time, 1 software-pipelined
   int32_t pad_;
+  // Per-plane closing of the u8 bulk-copy ring kernel (plans): with fin_cnt
+  // set, the kernel's SSE pointer is an accumulator and fin_cnt a count of
+  // finished units per plane slot, both zero at launch; the warp that
+  // finishes a plane's last units moves its SSE to fin_sse, writes its PSNR
+  // to fin_psnr (if set) and leaves both at zero for the next launch.
+  unsigned long long* fin_sse;
+  double* fin_psnr;
+  unsigned int* fin_cnt;
 };
 
 // Forward, zonal mask, scale by q_i q_j, inverse, round and clamp one block.
@@ -1075,6 +1083,30 @@ __host__ __device__ constexpr int ring_unit_bytes() {
   return SHIFT ? kRingUnitBytes : kUnitBytes;
 }
 
+// Per-plane closing (cp.fin_cnt set), run by one lane for a warp that has
+// finished `units` of the `total` units of the plane in `slot`, with SSE
+// partial sum v: add v, then (after a fence) the units; the call that brings
+// the count to `total` has every other warp's sum in the accumulator, moves
+// it to fin_sse with PSNR = 10 log10(255^2 npix / SSE) (+inf for SSE = 0,
+// §6.1) and leaves accumulator and count at zero.  No warp waits for another.
+// Not inlined: it keeps the main loop's register allocation.
+static __device__ __noinline__ void close_plane_units(int slot, int64_t npix,
+                                                      unsigned long long v, unsigned int units,
+                                                      unsigned int total,
+                                                      unsigned long long* acc,
+                                                      const CodecParams& cp) {
+  if (v) atomicAdd(acc + slot, v);
+  __threadfence();
+  if (atomicAdd(cp.fin_cnt + slot, units) + units != total) return;
+  __threadfence();
+  const unsigned long long sse = atomicExch(acc + slot, 0ull);
+  atomicExch(cp.fin_cnt + slot, 0u);
+  cp.fin_sse[slot] = sse;
+  if (cp.fin_psnr)
+    cp.fin_psnr[slot] =
+        sse == 0ull ? (double)INFINITY : 10.0 * log10(65025.0 * (double)npix / (double)sse);
+}
+
 // WRAP: the launch's planes have units that run on across block rows (64
 // consecutive blocks in raster order; vec16 bit 5): at most two row segments
 // per unit, because such planes are at least 64 blocks wide.  The ring row k
@@ -1229,16 +1261,30 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
   int p = -1;
   int p_end = -1;
   PlaneDesc P;
+  unsigned long long acc = 0;
+  // The warp's SSE of plane p so far: added to the plane's accumulator, and
+  // with per-plane closing (plans) also the warp's units of the plane.
+  auto flush_plane = [&]() {
+    acc = warp_sum_u64(acc);
+    if (cp.fin_cnt) {
+      if (lane == 0) {
+        const int64_t first = P.unit_begin - u_begin;
+        const int64_t end = (p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U;
+        close_plane_units(P.slot, (int64_t)P.H * P.W, acc,
+                          (unsigned int)(p_end - (first > 0 ? first : 0)),
+                          (unsigned int)(end - P.unit_begin), sse_out, cp);
+      }
+    } else if (lane == 0 && acc) {
+      atomicAdd(sse_out + P.slot, acc);
+    }
+    acc = 0;
+  };
   int by = 0, chunk = 0, s = 0;  // consumer cursor, advanced like the producer's
   int64_t rem = 0;               // WRAP: as pp_rem (chunk: the unit's first block column)
-  unsigned long long acc = 0;
+  bool failed = false;
   for (int i = 0; i < n_units; ++i) {
     if (i >= p_end) {
-      if (p >= 0) {
-        acc = warp_sum_u64(acc);
-        if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
-        acc = 0;
-      }
+      if (p >= 0) flush_plane();
       const int64_t u = u_begin + i;
       p = find_plane(tab, u);
       P = tab.d ? tab.d[p] : tab.one;
@@ -1269,7 +1315,10 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
         ++by;
       }
       s = s + 1 == STAGES ? 0 : s + 1;
-      if (!wait_slot(cur_s)) return;
+      if (!wait_slot(cur_s)) {
+        failed = true;
+        break;
+      }
       const uint8_t* slot = ring + cur_s * UB + lane * 16;
       if (has)
         acc += codec_pair_u8<R, true>(P, lby, lbx, RowsInSmem{slot}, RowsInSmem{slot + 8}, cp);
@@ -1284,7 +1333,10 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
       ++by;
     }
     s = s + 1 == STAGES ? 0 : s + 1;
-    if (!wait_slot(cur_s)) return;
+    if (!wait_slot(cur_s)) {
+      failed = true;
+      break;
+    }
     // the lane's two blocks stay in the slot: the forward reads them, the
     // epilogue reads them again for the SSE; the slot is refilled after
     const uint8_t* slot = ring + cur_s * UB + lane * 16;
@@ -1300,9 +1352,21 @@ __global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
     __syncwarp();
     if (pf < n_units) issue_next();  // refill the slot just used
   }
-  if (p >= 0) {
-    acc = warp_sum_u64(acc);
-    if (lane == 0 && acc) atomicAdd(sse_out + P.slot, acc);
+  // A warp whose wait gave up flushes its partial sum (the status word
+  // reports the launch as incomplete); with per-plane closing it still
+  // counts every unit of its range, so that each plane closes and leaves
+  // its accumulator at zero.
+  if (p >= 0) flush_plane();
+  if (failed && cp.fin_cnt) {
+    for (int i = p_end; i < n_units;) {
+      const int64_t u = u_begin + i;
+      p = find_plane(tab, u);
+      P = tab.d ? tab.d[p] : tab.one;
+      const int64_t e = ((p + 1 < tab.n) ? tab.d[p + 1].unit_begin : U) - u_begin;
+      p_end = (int)(e < n_units ? e : n_units);
+      flush_plane();
+      i = p_end;
+    }
   }
 }
 

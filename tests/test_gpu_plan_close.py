@@ -1,0 +1,127 @@
+"""Plans whose launches all run the u8 bulk-copy ring kernel close each launch
+inside that kernel: the CTA that finishes last writes every plane's SSE and
+PSNR (§6.1) and leaves the plan's accumulators at zero, so the graph holds
+the codec launches only (no reset of the SSE array, no PSNR kernel).
+
+Checked against the oracle over repeated launches with garbage left in the
+output arrays, with PSNR on and off, over several groups (block-row units,
+units across block rows, rows 8 mod 16), for a plane whose SSE is 0
+(PSNR +inf), and after a launch whose bounded wait gave up (the next launch
+is exact: that launch still reset the accumulators)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1808_02950_gb300 as P
+from oracle import codec as oc
+from oracle import matrices as M
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _planes(seed):
+    rng = np.random.default_rng(seed)
+    shapes = [(64, 1024, 16), (64, 1088, 16), (64, 1032, 4), (128, 512, 8), (64, 1024, 8),
+              (200, 2048, 16), (64, 1088, 32)]
+    hosts = [rng.integers(0, 256, (H, W)).astype(np.uint8) for H, W, _ in shapes]
+    hosts.append(np.full((64, 1024), 77, np.uint8))  # a flat plane: SSE 0
+    rs = [r for _, _, r in shapes] + [16]
+    views = [torch.from_numpy(h).to(DEV) for h in hosts]
+    return hosts, views, rs
+
+
+def _want(hosts, rs):
+    return [oc.codec_plane(h, M.T1, r) for h, r in zip(hosts, rs)]
+
+
+def test_self_closing_plan_matches_oracle_over_repeats():
+    hosts, views, rs = _planes(5)
+    recons = [torch.full_like(v, 3) for v in views]
+    planes = P.make_planes(views, rs, recons)
+    plan = P.tdct_plan_create(planes, path=P.TDCT_PATH_BUTTERFLY)
+    try:
+        groups = plan.groups()
+        assert all(g["dtype"] == "u8" and g["load"] == "bulk" for g in groups)
+        assert len(groups) >= 4
+        assert plan.kernel_count() == len(groups)  # codec launches only
+        want = _want(hosts, rs)
+        assert want[-1][0] == 0
+        n = len(views)
+        sse = torch.empty(n, dtype=torch.int64, device=DEV)
+        psnr = torch.empty(n, dtype=torch.float64, device=DEV)
+        for rep in range(3):
+            sse.fill_(-1 - rep)
+            psnr.fill_(-7.0)
+            plan.launch(sse, psnr)
+            torch.cuda.synchronize()
+            for i, (s, rec, _) in enumerate(want):
+                assert int(sse[i]) == s, (rep, i)
+                p = float(psnr[i])
+                if s == 0:
+                    assert math.isinf(p) and p > 0
+                else:
+                    assert p == pytest.approx(oc.psnr(s, hosts[i].size), rel=1e-12)
+                assert np.array_equal(recons[i].cpu().numpy(), rec), (rep, i)
+        # without PSNR, then again with it into other arrays
+        sse2 = torch.full((n,), 123, dtype=torch.int64, device=DEV)
+        plan.launch(sse2)
+        sse3 = torch.full((n,), 5, dtype=torch.int64, device=DEV)
+        psnr3 = torch.zeros(n, dtype=torch.float64, device=DEV)
+        plan.launch(sse3, psnr3)
+        torch.cuda.synchronize()
+        assert [int(v) for v in sse2.cpu()] == [w[0] for w in want]
+        assert [int(v) for v in sse3.cpu()] == [w[0] for w in want]
+        assert np.array_equal(psnr3.cpu().numpy(), psnr.cpu().numpy())
+    finally:
+        plan.close()
+
+
+def test_mixed_plan_keeps_the_reset_and_psnr_kernel():
+    """An int16 plane in the batch: its group runs another kernel, so the plan
+    keeps the SSE reset and the PSNR kernel (one more launch)."""
+    hosts, views, rs = _planes(6)
+    rng = np.random.default_rng(6)
+    res = rng.integers(-255, 256, (64, 512)).astype(np.int16)
+    views = views + [torch.from_numpy(res).to(DEV)]
+    hosts = hosts + [res]
+    rs = rs + [8]
+    plan = P.tdct_plan_create(P.make_planes(views, rs), path=P.TDCT_PATH_BUTTERFLY)
+    try:
+        assert plan.kernel_count() == len(plan.groups()) + 1
+        sse = torch.full((len(views),), -1, dtype=torch.int64, device=DEV)
+        plan.launch(sse)
+        torch.cuda.synchronize()
+        want = [oc.codec_plane(h, M.T1, r, want_recon=False)[0] for h, r in zip(hosts, rs)]
+        assert [int(v) for v in sse.cpu()] == want
+    finally:
+        plan.close()
+
+
+def test_self_closing_plan_after_a_timed_out_launch():
+    hosts, views, rs = _planes(7)
+    want = [s for s, _, _ in _want(hosts, rs)]
+    n = len(views)
+    P.tdct_sync_status()  # clean start
+    P.tdct_debug_inject_wait_timeout(True)
+    plan = P.tdct_plan_create(P.make_planes(views, rs), path=P.TDCT_PATH_BUTTERFLY)
+    try:
+        assert plan.kernel_count() == len(plan.groups())
+        bad = torch.zeros(n, dtype=torch.int64, device=DEV)
+        plan.launch(bad)  # captured with the withheld copy
+        with pytest.raises(P.TdctError) as e:
+            P.tdct_sync_status()
+        assert e.value.code == 4  # TDCT_ETIMEOUT
+        P.tdct_sync_status()
+        # new output arrays: a new capture, without the hook
+        sse = torch.full((n,), -1, dtype=torch.int64, device=DEV)
+        psnr = torch.zeros(n, dtype=torch.float64, device=DEV)
+        plan.launch(sse, psnr)
+        torch.cuda.synchronize()
+        assert [int(v) for v in sse.cpu()] == want
+        P.tdct_sync_status()
+    finally:
+        P.tdct_debug_inject_wait_timeout(False)
+        plan.close()
