@@ -225,6 +225,7 @@ CodecParams make_params(int r, int ctas_per_sm = 0, int tc_variant = 0) {
     for (int j = 0; j < 8; ++j) {
       cp.cmul[8 * i + j] = kept(r, i, j) ? q_of(i) * q_of(j) : 0;
       cp.cmul2[8 * i + j] = 2 * cp.cmul[8 * i + j];
+      cp.cmul2h[8 * i + j] = cp.cmul2[8 * i + j] * 65536;
     }
   cp.status = status_word();
   cp.wait_limit = 2000000000ll;  // about a second of SM clock

@@ -159,6 +159,7 @@ __device__ __forceinline__ void reconstruct(uint32_t w[64], int32_t out[64]) {
 struct CodecParams {
   int32_t cmul[64];
   int32_t cmul2[64];
+  int32_t cmul2h[64];    // cmul2 * 2^16 (< 2^31): block B's scaled coefficient in one multiply-high
   int* status;           // device status word (TDCT_ETIMEOUT on a bounded wait giving up)
   long long wait_limit;  // clock cycles a bulk-copy wait may take before giving up
   int32_t test_hook;     // 1: the first copy of warp 0 is never issued (timeout test)
@@ -794,6 +795,21 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8_any(const uint32_t w[64]
 #define TDCT_FWD_ROWS_FIRST_ON_TIE 1
 #endif
 
+// Classes whose bulk-copy ring kernel runs 4 CTAs per SM at 128 registers
+// (16 warps, 4 per scheduler) instead of 3 at 168: the kernel is bound by
+// dependency latency there, and forming both blocks' scaled coefficients
+// right after the forward (block B's by one multiply-high each) is what fits
+// it in 128 registers without spills.  Measured on GB300 (512 or 1024
+// images 1024x1024): 3-4 % faster at classes 15-21; slower at class 8, equal
+// at 32 (those keep 3 CTAs).
+#ifndef TDCT_RING_FOUR_CTAS
+#define TDCT_RING_FOUR_CTAS 1
+#endif
+template <int R>
+__host__ __device__ constexpr bool ring_four_ctas() {
+  return TDCT_RING_FOUR_CTAS && (R == 15 || R == 16 || R == 21 || R == 28);
+}
+
 // Both blocks of a lane (samples already in registers, zero outside the
 // plane) through the packed forward and the per-block inverse.
 // FULL: the caller guarantees both blocks exist, lie inside the plane and
@@ -861,6 +877,21 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
   const int64_t rp = P.recon_pitch;
   uint2* out0 = store ? reinterpret_cast<uint2*>(P.recon + (int64_t)(by * 8) * rp + (int64_t)bx0 * 8)
                       : nullptr;
+  // 4-CTA classes: both blocks' scaled coefficients before either inverse:
+  // block A's lane a times c in place of the packed word, block B's from
+  // v - a = 2^16 b (exact), as mulhi(2^16 b, 2^16 c) = b c; the packed words
+  // die here, which keeps the inverse within 128 registers
+  uint32_t w1[64];
+  if constexpr (ring_four_ctas<R>()) {
+#pragma unroll
+    for (int p = 0; p < 64; ++p) {
+      if (kept(R, p >> 3, p & 7)) {
+        const int32_t lo = lane_lo(z[p]);
+        w1[p] = (uint32_t)__mulhi((int32_t)(z[p] - (uint32_t)lo), cp.cmul2h[p]);
+        z[p] = (uint32_t)lo * (uint32_t)cp.cmul2[p];
+      }
+    }
+  }
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
     if (b == 1 && !has1) break;
@@ -871,8 +902,12 @@ __device__ __forceinline__ uint32_t codec_pair_u8(const PlaneDesc& P, int by, in
       for (int j = 0; j < 8; ++j) {
         const int p = 8 * i + j;
         if (kept(R, i, j)) {
-          const int32_t zz = b == 0 ? lane_lo(z[p]) : lane_hi(z[p]);
-          w[p] = (uint32_t)zz * (uint32_t)cp.cmul2[p];
+          if constexpr (ring_four_ctas<R>()) {
+            w[p] = b == 0 ? z[p] : w1[p];
+          } else {
+            const int32_t zz = b == 0 ? lane_lo(z[p]) : lane_hi(z[p]);
+            w[p] = (uint32_t)zz * (uint32_t)cp.cmul2[p];
+          }
         } else {
           w[p] = 0u;
         }
@@ -1069,7 +1104,7 @@ __host__ __device__ constexpr int ring_min_blocks() {
 #ifdef TDCT_RING_MINB
   return TDCT_RING_MINB;
 #else
-  return R >= 36 ? 2 : 3;
+  return R >= 36 ? 2 : ring_four_ctas<R>() ? 4 : 3;
 #endif
 }
 
@@ -1408,8 +1443,10 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// (3 CTAs per SM below class 36 whatever ring_four_ctas says: at 128
+// registers this kernel spills at class 21)
 template <int R, int STAGES>
-__global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
+__global__ void __launch_bounds__(TDCT_RING_THREADS, R >= 36 ? 2 : 3)
     codec_u8_staged_kernel(const PlaneTable tab, const CodecParams cp,
                            unsigned long long* __restrict__ sse_out) {
   extern __shared__ __align__(128) uint8_t smem[];
