@@ -795,13 +795,14 @@ __device__ __forceinline__ uint32_t inverse_epilogue_u8_any(const uint32_t w[64]
 #define TDCT_FWD_ROWS_FIRST_ON_TIE 1
 #endif
 
-// Classes whose bulk-copy ring kernel runs 4 CTAs per SM at 128 registers
-// (16 warps, 4 per scheduler) instead of 3 at 168: the kernel is bound by
-// dependency latency there, and forming both blocks' scaled coefficients
-// right after the forward (block B's by one multiply-high each) is what fits
-// it in 128 registers without spills.  Measured on GB300 (512 or 1024
-// images 1024x1024): 3-4 % faster at classes 15-21; slower at class 8, equal
-// at 32 (those keep 3 CTAs).
+// Classes whose bulk-copy ring kernel (rows 16-byte aligned, units within a
+// block row) runs 4 CTAs per SM at 128 registers (16 warps, 4 per
+// scheduler) instead of 3 at 168: the kernel is bound by dependency latency
+// there, and forming both blocks' scaled coefficients right after the
+// forward (block B's by one multiply-high each) is what fits it in 128
+// registers without spills.  Measured on GB300 (512 or 1024 images
+// 1024x1024): 3-4 % faster at classes 15-21; slower at class 8, equal at 32
+// (those keep 3 CTAs).
 #ifndef TDCT_RING_FOUR_CTAS
 #define TDCT_RING_FOUR_CTAS 1
 #endif
@@ -1099,12 +1100,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 #define TDCT_RING_THREADS 128
 #endif
 
-template <int R>
+// Resident CTAs per SM the bulk-copy ring kernel is compiled for; the
+// shifted-row and row-wrapping variants keep 3 (their 16-warp builds measured
+// 2-4 % slower on the ragged batch).
+template <int R, bool SHIFT = false, bool WRAP = false>
 __host__ __device__ constexpr int ring_min_blocks() {
 #ifdef TDCT_RING_MINB
   return TDCT_RING_MINB;
 #else
-  return R >= 36 ? 2 : ring_four_ctas<R>() ? 4 : 3;
+  return R >= 36 ? 2 : (ring_four_ctas<R>() && !SHIFT && !WRAP) ? 4 : 3;
 #endif
 }
 
@@ -1152,7 +1156,7 @@ static __device__ __noinline__ void close_plane_units(int slot, int64_t npix,
 // whose width is not a multiple of 64 blocks then leaves no nearly empty unit
 // behind, which at the compute-bound r cost a warp nearly a full unit.
 template <int R, int STAGES, bool SHIFT = false, bool WRAP = false>
-__global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R>())
+__global__ void __launch_bounds__(TDCT_RING_THREADS, ring_min_blocks<R, SHIFT, WRAP>())
     codec_u8_tma_kernel(const PlaneTable tab, const CodecParams cp,
                         unsigned long long* __restrict__ sse_out) {
   constexpr int UB = ring_unit_bytes<SHIFT>();
