@@ -1,7 +1,8 @@
-"""Plans whose launches all run the u8 bulk-copy ring kernel close each launch
-inside that kernel: the CTA that finishes last writes every plane's SSE and
-PSNR (§6.1) and leaves the plan's accumulators at zero, so the graph holds
-the codec launches only (no reset of the SSE array, no PSNR kernel).
+"""Plans whose launches all run the u8 bulk-copy ring kernel close their
+planes inside that kernel: the warp that finishes a plane's last units writes
+its SSE and PSNR (§6.1) and leaves the plan's per-plane accumulators at zero,
+so the graph holds the codec launches only (no reset of the SSE array, no
+PSNR kernel).
 
 Checked against the oracle over repeated launches with garbage left in the
 output arrays, with PSNR on and off, over several groups (block-row units,
@@ -124,4 +125,38 @@ def test_self_closing_plan_after_a_timed_out_launch():
         P.tdct_sync_status()
     finally:
         P.tdct_debug_inject_wait_timeout(False)
+        plan.close()
+
+
+def test_self_closing_plan_many_small_planes():
+    """Hundreds of small planes (one or a few units each), so that most warps
+    close several planes and most planes are closed by another warp than the
+    one that started them; repeated launches stay exact."""
+    rng = np.random.default_rng(11)
+    shapes = [(8, 16), (16, 32), (8, 1024), (64, 64), (24, 528), (8, 16 * 65)]
+    hosts, rs = [], []
+    for i in range(600):
+        H, W = shapes[i % len(shapes)]
+        hosts.append(rng.integers(0, 256, (H, W)).astype(np.uint8))
+        rs.append(int(rng.choice([1, 8, 16, 21])))
+    views = [torch.from_numpy(h).to(DEV) for h in hosts]
+    recons = [torch.zeros_like(v) for v in views]
+    plan = P.tdct_plan_create(P.make_planes(views, rs, recons), path=P.TDCT_PATH_BUTTERFLY)
+    try:
+        assert plan.kernel_count() == len(plan.groups())
+        want = _want(hosts, rs)
+        n = len(views)
+        for rep in range(2):
+            sse = torch.full((n,), -1, dtype=torch.int64, device=DEV)
+            psnr = torch.zeros(n, dtype=torch.float64, device=DEV)
+            plan.launch(sse, psnr)
+            torch.cuda.synchronize()
+            got = sse.cpu().numpy()
+            gp = psnr.cpu().numpy()
+            for i, (s, rec, _) in enumerate(want):
+                assert int(got[i]) == s, (rep, i)
+                assert gp[i] == pytest.approx(oc.psnr(s, hosts[i].size), rel=1e-12)
+        for i in range(0, n, 37):
+            assert np.array_equal(recons[i].cpu().numpy(), want[i][1]), i
+    finally:
         plan.close()
